@@ -1,0 +1,191 @@
+/*
+ * rbd.h -- C ABI of the GB300 (sm_103a) Reduced Basis Decomposition library, librbd.so.
+ *
+ * Reduced Basis Decomposition (Y. Chen, "Reduced Basis Decomposition: a Certified and Fast
+ * Lossy Data Compression Algorithm", arXiv 1503.05947) approximates a data matrix
+ * X in R^{m x n} by Y T, Y in R^{m x d} with orthonormal columns and T in R^{d x n}, through
+ * the greedy loop of Algorithm 1 (Section 3.1).  Every step of that loop runs in this
+ * library's CUDA kernels on the GPU; nothing falls back to the CPU.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are COLUMN-MAJOR with an explicit leading dimension (ld >= number of rows):
+ *     element (r, c) of a matrix A with leading dimension lda is A[r + c * lda].
+ *     Column j of X is the data entry X(:, j) of Section 3.1.
+ *   - Indices are 0-based (the paper counts from 1).
+ *   - Unless stated otherwise, array pointers are DEVICE pointers owned by the caller; the
+ *     library neither frees nor keeps them after the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  All
+ *     device work of a call is ordered on that stream.
+ *   - Errors are returned as rbd_status codes.  No call aborts, traps or throws.  Device-side
+ *     conditions (non-finite input, a bounded wait that ran out) are reported through the
+ *     status of the call that launched the kernels; such a call synchronises `stream`.
+ *   - The library is not re-entrant on a single stream for overlapping calls that share a
+ *     workspace; distinct workspaces on distinct streams may run concurrently.
+ */
+#ifndef RBD_H
+#define RBD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rbd_status {
+    RBD_OK = 0,
+    RBD_EINVAL = 1,        /* an argument is out of range, NULL where required, or misaligned */
+    RBD_ENOMEM = 2,        /* device or pinned host allocation failed, or workspace too small */
+    RBD_ECUDA = 3,         /* a CUDA runtime call failed (launch error, bad stream, ...) */
+    RBD_ENONFINITE = 4,    /* X holds a NaN or an infinity */
+    RBD_ETIMEOUT = 5,      /* a bounded device-side wait ran out (the kernel returned early) */
+    RBD_EUNSUPPORTED = 6   /* a value outside the supported range (|x| >= 2^127 in the FP64
+                              form), or a shape the kernels do not support */
+} rbd_status;
+
+/* Storage type of X (and of out-of-sample vectors).  Y, T and all indicators are FP64. */
+typedef enum rbd_dtype {
+    RBD_F64 = 0,
+    RBD_F32 = 1,
+    RBD_BF16 = 2
+} rbd_dtype;
+
+/* How the tolerance `tol` of Algorithm 1 (epsilon_R) is applied. */
+typedef enum rbd_tol_mode {
+    /* Algorithm 1 as printed: step 2.4 stops when E_cur = max_j ||X(:,j) - Y T(:,j)|| <= tol,
+       step 2.2 breaks when the orthogonalised pivot has ||v|| < tol. */
+    RBD_TOL_MAXCOL_ABS = 0,
+    /* the same with epsilon_R = tol * max_j ||X(:,j)||. */
+    RBD_TOL_MAXCOL_REL = 1,
+    /* step 2.4 stops when ||X - Y T||_F <= tol * ||X||_F (the Frobenius error is the square
+       root of the sum of the per-column squared residuals); step 2.2 breaks when
+       ||v|| < tol * ||X||_F / sqrt(n). */
+    RBD_TOL_FRO_REL = 2
+} rbd_tol_mode;
+
+/* Why the greedy loop ended. */
+typedef enum rbd_stop_reason {
+    RBD_STOP_NONE = 0,
+    RBD_STOP_TOL = 1,      /* step 2.4: the error indicator reached the tolerance */
+    RBD_STOP_BREAK = 2,    /* step 2.2: the next pivot's orthogonalised norm was below the
+                              tolerance, or below the numerical-rank floor (RBD_RANK_FLOOR) */
+    RBD_STOP_DMAX = 3      /* d reached d_max */
+} rbd_stop_reason;
+
+/* Step 2.2 also breaks when ||v|| <= RBD_RANK_FLOOR * ||X(:, i)|| for the pivot column i:
+   such a column already lies in span(Y) up to rounding, and normalising it would add a basis
+   vector made of rounding noise (the paper's test alone never fires when tol = 0). */
+#define RBD_RANK_FLOOR 1e-12
+
+/* Summary written to host memory by rbd_compress / rbd_compress_host. */
+typedef struct rbd_result {
+    int64_t d;            /* number of bases produced (columns of Y, rows of T) */
+    int64_t next_pivot;   /* argmax of the last step 2.3: the column the next basis would use */
+    int32_t stop_reason;  /* an rbd_stop_reason */
+    int32_t launches;     /* kernels this call launched */
+    double err_last;      /* E_cur after the last basis (max column residual), 0 if d = 0 */
+    double fro_last;      /* ||X - Y T||_F after the last basis, from the summed indicators */
+    double x_fro;         /* ||X||_F */
+    double x_maxcol;      /* max_j ||X(:, j)|| */
+} rbd_result;
+
+/* Bytes of device workspace rbd_compress needs for these sizes (0 on invalid sizes).
+   The workspace holds the re-laid-out X (the same number of bytes as an FP64 X for
+   RBD_F64, as the input for RBD_F32/RBD_BF16, with columns padded to 128 rows), one split
+   FP32 copy of Y, and O(m + n + d_max) vectors. */
+size_t rbd_compress_workspace_bytes(int64_t m, int64_t n, int64_t d_max, rbd_dtype xt);
+
+/*
+ * rbd_compress -- Algorithm 1 of Section 3.1: (Y, T) = RBD(X, epsilon_R, d_max).
+ *
+ *  X       [in]  device, m x n column-major, leading dimension ldx >= m, storage type xt.
+ *                Read only.  For RBD_F64 every element must satisfy |x| < 2^127.
+ *  tol     [in]  epsilon_R >= 0, interpreted according to `mode`.
+ *  d_max   [in]  1 <= d_max <= min(m, n): capacity of the outputs and the loop limit.
+ *  start   [in]  0 <= start < n: the column of step 1 (the paper draws it at random or takes a
+ *                user input; pass a random index for the paper's behaviour).
+ *  Y       [out] device, m x d_max, column-major, ldy >= m.  Y(:, k) = xi_k.
+ *  T       [out] device, d_max x n, column-major, ldt >= d_max.  T(k, :) = xi_k' X.
+ *  pivots  [out] device, d_max int64: pivots[k] = the column of X that gave xi_k.
+ *  err     [out] device, d_max doubles: err[k] = E_cur of step 2.3 after basis k,
+ *                max_j ||X(:, j) - Y(:, 0:k) T(0:k, j)||, evaluated through Eq. (evalerr)
+ *                with A = I (squared column norm minus the squared coefficients, FP64).
+ *  nu      [out] device, d_max doubles, or NULL: nu[k] = ||v|| of step 2.2 for basis k, the
+ *                FP64 residual of column pivots[k] against bases 0..k-1 recomputed from X.
+ *  workspace, workspace_bytes
+ *          [in]  device scratch of at least rbd_compress_workspace_bytes(m, n, d_max, xt)
+ *                bytes, 256-byte aligned; or NULL/0, in which case the call allocates it
+ *                stream-ordered (cudaMallocAsync) and frees it before returning.
+ *  stream  [in]  cudaStream_t as void*.
+ *  result  [out] host, or NULL: summary (d, stop reason, last indicator, norms of X).
+ *
+ *  Only the first `d` columns of Y, rows of T and entries of pivots/err/nu are written.
+ *  The call synchronises `stream` once at the end (to learn d); every step of the loop is
+ *  ordered on `stream` without host round trips.
+ *  Errors: RBD_EINVAL for bad sizes, leading dimensions, start, tol, mode, dtype or NULL
+ *  outputs; RBD_ENOMEM if the workspace is too small or cannot be allocated;
+ *  RBD_ENONFINITE if X holds NaN/Inf; RBD_EUNSUPPORTED for |x| >= 2^127 in the FP64 form;
+ *  RBD_ETIMEOUT / RBD_ECUDA for device failures.  On error the outputs are unspecified.
+ */
+rbd_status rbd_compress(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
+                        double tol, rbd_tol_mode mode, int64_t d_max, int64_t start,
+                        double* Y, int64_t ldy, double* T, int64_t ldt,
+                        int64_t* pivots, double* err, double* nu,
+                        void* workspace, size_t workspace_bytes,
+                        void* stream, rbd_result* result);
+
+/*
+ * rbd_compress_host -- rbd_compress on HOST buffers (end-to-end form).
+ *
+ * Same arguments and layout as rbd_compress, but X, Y, T, pivots, err and nu (nu may be
+ * NULL) are HOST pointers.  The call allocates device buffers stream-ordered, copies X to
+ * the device, runs the loop, copies the first d columns/rows/entries back and frees the
+ * device buffers.  Pinned host buffers make the copies asynchronous DMA transfers; pageable
+ * ones work but are staged by the driver.  Returns after the results are in host memory.
+ */
+rbd_status rbd_compress_host(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
+                             double tol, rbd_tol_mode mode, int64_t d_max, int64_t start,
+                             double* Y, int64_t ldy, double* T, int64_t ldt,
+                             int64_t* pivots, double* err, double* nu,
+                             void* stream, rbd_result* result);
+
+/*
+ * rbd_project -- the out-of-sample map of Section 3.1, v_C = Y' v, for k vectors at once:
+ * C = Y' V.
+ *
+ *  Y  [in]  device, m x d FP64 column-major, ldy >= m (orthonormal columns from rbd_compress).
+ *  V  [in]  device, m x k column-major, ldv >= m, storage type vt.
+ *  C  [out] device, d x k FP64 column-major, ldc >= d.
+ *  d = 0 or k = 0 is a no-op.  Stream-ordered; does not synchronise.  Dot products are
+ *  evaluated with FP64-grade (float-float, relative error below 2^-44) accuracy.
+ *  Errors: RBD_EINVAL for bad sizes/leading dimensions/NULL; RBD_ECUDA on launch failure.
+ */
+rbd_status rbd_project(const double* Y, int64_t m, int64_t d, int64_t ldy,
+                       const void* V, rbd_dtype vt, int64_t k, int64_t ldv,
+                       double* C, int64_t ldc, void* stream);
+
+/* Per-kernel timing of the most recent rbd_compress call on this host thread, taken with
+   CUDA events recorded on the call's stream around each launch when profiling is enabled
+   (rbd_set_profiling(1)).  Times are in milliseconds. */
+typedef struct rbd_profile {
+    int64_t pass_launches;   /* fused pass kernels (one per basis) */
+    double pass_ms;          /* their summed durations */
+    int64_t orth_launches;   /* orthogonalisation kernels */
+    double orth_ms;
+    double init_ms;          /* the initial norm / re-layout pass */
+    int64_t pass_bytes;      /* algorithmic bytes of X streamed by the pass kernels */
+} rbd_profile;
+
+void rbd_set_profiling(int enabled);
+rbd_status rbd_get_profile(rbd_profile* out);
+
+const char* rbd_status_string(rbd_status s);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int rbd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBD_H */

@@ -1,0 +1,21 @@
+"""GB300-native Reduced Basis Decomposition (Y. Chen, arXiv 1503.05947).
+
+The greedy compression X ~ Y T of Algorithm 1 runs in hand-written CUDA kernels for sm_103a
+behind the C ABI of include/rbd.h (librbd.so); ``rbd`` is its thin Python binding.
+"""
+from .rbd import (  # noqa: F401
+    Compressed,
+    RbdError,
+    as_colmajor,
+    colmajor_empty,
+    compress,
+    compress_host,
+    get_profile,
+    load,
+    project,
+    set_profiling,
+    status_string,
+    version,
+    workspace_bytes,
+)
+from .buildlib import build  # noqa: F401

@@ -1,0 +1,212 @@
+// rbd_device.cuh -- device-side building blocks shared by the librbd kernels.
+//
+//  * float-float ("ff") arithmetic: an FP64-grade quantity carried as the unevaluated sum
+//    hi + lo of two FP32 numbers.  GB300 executes FP64 FMAs at ~1/64 of the FP32 rate
+//    (measured: 0.59 T DFMA/s against 34.9 T FFMA/s), too slow to keep up with HBM on the
+//    passes over X, so those passes run on the FP32 pipes with error-free transformations:
+//    TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and the FMA-based exact product (the product a*b
+//    and its rounding error fma(a, b, -a*b)).  Sums of float-float products have relative
+//    error ~2^-47, far inside the 1e-10 parity budget; FP64 is used for the per-column and
+//    per-step scalars (coefficients, squared residuals, norms).
+//  * inline PTX for mbarriers and the Blackwell bulk-copy (TMA) engine, with every wait
+//    bounded in time so that no kernel can spin forever.
+//  * the control block shared by the kernels of one rbd_compress call.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rbd {
+
+// --------------------------------------------------------------------------------------
+// Status / stop codes (mirror include/rbd.h)
+// --------------------------------------------------------------------------------------
+enum : int32_t { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENONFINITE = 4,
+                 ST_ETIMEOUT = 5, ST_EUNSUPPORTED = 6 };
+enum : int32_t { STOP_NONE = 0, STOP_TOL = 1, STOP_BREAK = 2, STOP_DMAX = 3 };
+enum : int32_t { MODE_MAXCOL_ABS = 0, MODE_MAXCOL_REL = 1, MODE_FRO_REL = 2 };
+
+// Step 2.2 treats a pivot whose orthogonalised norm is at most kRankFloor * ||X(:, i)|| as
+// already in span(Y) (numerical-rank floor; matches RBD_RANK_FLOOR in rbd.h).
+constexpr double kRankFloor = 1e-12;
+
+// Upper bound on any device-side wait (nanoseconds of %globaltimer).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// --------------------------------------------------------------------------------------
+// Control block: one per rbd_compress call, in device workspace.
+// --------------------------------------------------------------------------------------
+struct Ctl {
+    int64_t d;            // bases accepted so far (the step being built has index d)
+    int64_t pivot;        // column orthogonalised in the current step (step 2.1's i)
+    int32_t stop;         // STOP_*; once non-zero every later kernel returns at entry
+    int32_t status;       // ST_* raised on the device
+    uint32_t pass_arrive; // last-arriver counters (reset to 0 by the last arriver)
+    uint32_t c_arrive;
+    uint32_t init_arrive;
+    uint32_t pad0;
+    double nu;            // ||v|| of step 2.2 for the current step
+    double inv_nu;        // 1 / nu
+    double eps_r;         // step 2.4 threshold on E_cur (MAXCOL modes)
+    double eps_r22;       // step 2.2 threshold on ||v||
+    double fro_tol;       // FRO mode: tol * ||X||_F, else -1
+    double x_fro;         // ||X||_F
+    double x_maxcol;      // max_j ||X(:, j)||
+    double err_downdate;  // sqrt(max_j e_j) of the last pass (Eq. (evalerr) form, diagnostic)
+    double err_last;      // certified E_cur after the last accepted basis
+    double fro_last;      // ||X - Y T||_F after the last accepted basis
+    double tol;           // the user's tol
+    int32_t mode;         // MODE_*
+    int32_t pad1;
+    int64_t d_max;
+};
+
+// --------------------------------------------------------------------------------------
+// float-float helpers
+// --------------------------------------------------------------------------------------
+// s + e == a + b exactly (TwoSum; no precondition on |a|, |b|).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, c) += (xh + xl) * (yh + yl), dropping xl * yl (relative size <= 2^-48).
+// The leading product xh * yh is split exactly into p + pe; the cross terms are small and
+// are accumulated with pe into the compensation c.
+__device__ __forceinline__ void ff_mac2(float& s, float& c, float xh, float xl, float yh, float yl) {
+    float p = __fmul_rn(xh, yh);
+    float pe = __fmaf_rn(xh, yh, -p);
+    pe = __fmaf_rn(xh, yl, pe);
+    pe = __fmaf_rn(xl, yh, pe);
+    float t, e;
+    two_sum(s, p, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+
+// (s, c) += x * (yh + yl) for an exact FP32 x.
+__device__ __forceinline__ void ff_mac1(float& s, float& c, float x, float yh, float yl) {
+    float p = __fmul_rn(x, yh);
+    float pe = __fmaf_rn(x, yh, -p);
+    pe = __fmaf_rn(x, yl, pe);
+    float t, e;
+    two_sum(s, p, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ double ff_to_double(float s, float c) {
+    return (double)s + (double)c;
+}
+
+// x ~= hi + lo with |x - hi - lo| <= 2^-48 |x| (for |x| in the FP32 normal range).
+__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+}
+
+// --------------------------------------------------------------------------------------
+// warp reductions
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum_double(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// (value, index) max with ties to the lowest index; invalid entries carry index INT64_MAX.
+__device__ __forceinline__ bool better(double e1, int64_t j1, double e0, int64_t j0) {
+    return (e1 > e0) || (e1 == e0 && j1 < j0);
+}
+
+// --------------------------------------------------------------------------------------
+// PTX: shared-memory addresses, mbarriers, bulk copies, L2 policies, timers
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false if kWaitLimitNs elapsed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Bulk (TMA) copy global -> shared, completing `bytes` transaction bytes on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                         uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// Named barrier over `nthreads` threads (a multiple of 32) with id `id` (1..15).
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ void raise_status(Ctl* ctl, int32_t st) {
+    atomicCAS(&ctl->status, 0, st);
+}
+
+__host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+}  // namespace rbd

@@ -1,0 +1,188 @@
+// rbd_init.cu -- the initial pass over X (Section 3.3, "pre-computation of diag(X'AX)" with
+// A = I): e_j = ||X(:, j)||^2 for every column, ||X||_F and max_j ||X(:, j)|| for the
+// tolerance modes, and the one-time re-layout of X into the padded plane format the fused
+// pass streams with bulk copies (see rbd_work.h).
+#include "rbd_device.cuh"
+#include "rbd_work.h"
+
+namespace rbd {
+
+struct InitParams {
+    const void* X;
+    int64_t ldx, m, n, ldp;
+    void* planes;
+    double* e;
+    double* xn2;
+    Ctl* ctl;
+    double tol;
+    int mode;
+    int64_t start;
+    int64_t d_max;
+};
+
+// Split an FP64 value into FP32 hi + lo with integer operations only (no FP64 pipe):
+// hi keeps the sign, exponent and leading 24 significant bits (truncated); lo is the exact
+// remainder r * 2^(E-1075) (r < 2^29) rounded to 24 bits.  |x - hi - lo| <= 2^-48 |x|.
+// Values outside 2^-74 <= |x| < 2^127 take the FP64 conversion path.
+__device__ __forceinline__ void split_f64_fast(double x, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+    const int E = (int)((bh >> 20) & 0x7ffu);
+    if (E >= 949 && E <= 1149) {
+        const uint32_t sign = bh & 0x80000000u;
+        const uint32_t mant23 = ((bh & 0xfffffu) << 3) | (bl >> 29);
+        hi = __uint_as_float(sign | ((uint32_t)(E - 896) << 23) | mant23);
+        const uint32_t r = bl & 0x1fffffffu;
+        const float scale = __uint_as_float((uint32_t)(E - 948) << 23);  // 2^(E-1075)
+        lo = __uint_as_float(__float_as_uint(__fmul_rn(__uint2float_rn(r), scale)) | sign);
+    } else {
+        split_double(x, hi, lo);
+    }
+}
+
+template <int XT>
+__global__ void __launch_bounds__(256) init_kernel(InitParams p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int bad = ST_OK;
+    for (int64_t j = gw; j < p.n; j += nw) {
+        float s = 0.f, c = 0.f;
+        if (XT == 0) {  // FP64 -> two FP32 planes
+            const double* xj = (const double*)p.X + j * p.ldx;
+            float* ph = (float*)p.planes + j * p.ldp;
+            float* pl = (float*)p.planes + (p.n + j) * p.ldp;
+            for (int64_t r = lane; r < p.ldp; r += 32) {
+                const double x = (r < p.m) ? xj[r] : 0.0;
+                float hi, lo;
+                if (!isfinite(x)) {
+                    bad = ST_ENONFINITE;
+                    hi = lo = 0.f;
+                } else {
+                    if (fabs(x) >= 0x1p127) bad = (bad == ST_OK) ? ST_EUNSUPPORTED : bad;
+                    split_f64_fast(x, hi, lo);
+                }
+                ph[r] = hi;
+                pl[r] = lo;
+                ff_mac2(s, c, hi, lo, hi, lo);
+            }
+        } else if (XT == 1) {  // FP32 -> one FP32 plane
+            const float* xj = (const float*)p.X + j * p.ldx;
+            float* ph = (float*)p.planes + j * p.ldp;
+            for (int64_t r = lane; r < p.ldp; r += 32) {
+                float x = (r < p.m) ? xj[r] : 0.f;
+                if (!isfinite(x)) {
+                    bad = ST_ENONFINITE;
+                    x = 0.f;
+                }
+                ph[r] = x;
+                ff_mac1(s, c, x, x, 0.f);
+            }
+        } else {  // BF16 -> one BF16 plane
+            const __nv_bfloat16* xj = (const __nv_bfloat16*)p.X + j * p.ldx;
+            __nv_bfloat16* ph = (__nv_bfloat16*)p.planes + j * p.ldp;
+            for (int64_t r = lane; r < p.ldp; r += 32) {
+                __nv_bfloat16 xb = (r < p.m) ? xj[r] : __float2bfloat16(0.f);
+                float x = __bfloat162float(xb);
+                if (!isfinite(x)) {
+                    bad = ST_ENONFINITE;
+                    x = 0.f;
+                    xb = __float2bfloat16(0.f);
+                }
+                ph[r] = xb;
+                ff_mac1(s, c, x, x, 0.f);
+            }
+        }
+        const double t = warp_sum_double(ff_to_double(s, c));
+        if (lane == 0) {
+            p.e[j] = t;
+            p.xn2[j] = t;
+        }
+    }
+    if (bad != ST_OK) raise_status(p.ctl, bad);
+
+    // Last CTA to finish: column-norm statistics in a fixed order, and the tolerances.
+    __shared__ int s_last;
+    __shared__ double s_sum[256], s_max[256];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&p.ctl->init_arrive, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int64_t t = threadIdx.x, nt = blockDim.x;
+    const int64_t j0 = (p.n * t) / nt, j1 = (p.n * (t + 1)) / nt;
+    double sum = 0.0, mx = 0.0;
+    for (int64_t j = j0; j < j1; ++j) {
+        const double v = __ldcg(&p.xn2[j]);
+        sum += v;
+        mx = fmax(mx, v);
+    }
+    s_sum[t] = sum;
+    s_max[t] = mx;
+    __syncthreads();
+    for (int o = (int)nt / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            s_sum[t] += s_sum[t + o];
+            s_max[t] = fmax(s_max[t], s_max[t + o]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        Ctl* ctl = p.ctl;
+        const double fro = sqrt(s_sum[0]);
+        const double maxcol = sqrt(s_max[0]);
+        ctl->x_fro = fro;
+        ctl->x_maxcol = maxcol;
+        ctl->tol = p.tol;
+        ctl->mode = p.mode;
+        ctl->d_max = p.d_max;
+        if (p.mode == MODE_FRO_REL) {
+            ctl->fro_tol = p.tol * fro;  // compared with sqrt(sum of e_j)
+            ctl->eps_r = -1.0;
+            ctl->eps_r22 = p.tol * fro / sqrt((double)p.n);
+        } else {
+            const double eps = (p.mode == MODE_MAXCOL_REL) ? p.tol * maxcol : p.tol;
+            ctl->fro_tol = -1.0;
+            ctl->eps_r = eps;
+            ctl->eps_r22 = eps;
+        }
+        ctl->d = 0;
+        ctl->pivot = p.start;
+        ctl->err_last = 0.0;
+        ctl->fro_last = fro;
+        ctl->stop = (ctl->status != ST_OK) ? STOP_BREAK : STOP_NONE;
+        ctl->init_arrive = 0;
+    }
+}
+
+cudaError_t launch_init(const Work& w, const void* X, double tol, int mode, int64_t start,
+                        cudaStream_t st) {
+    InitParams p;
+    p.X = X;
+    p.ldx = w.ldx;
+    p.m = w.m;
+    p.n = w.n;
+    p.ldp = w.ldp;
+    p.planes = w.planes;
+    p.e = w.e;
+    p.xn2 = w.xn2;
+    p.ctl = w.ctl;
+    p.tol = tol;
+    p.mode = mode;
+    p.start = start;
+    p.d_max = w.d_max;
+    const int64_t warps = w.n;
+    int blocks = (int)ceil_div(warps, 8);
+    const int cap = w.num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    switch (w.xt) {
+        case 0: init_kernel<0><<<blocks, 256, 0, st>>>(p); break;
+        case 1: init_kernel<1><<<blocks, 256, 0, st>>>(p); break;
+        default: init_kernel<2><<<blocks, 256, 0, st>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rbd

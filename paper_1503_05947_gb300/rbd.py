@@ -1,0 +1,240 @@
+"""Python binding of librbd.so (include/rbd.h): argument marshalling only.
+
+Every step of Reduced Basis Decomposition runs in the library's CUDA kernels; this module only
+checks tensor layouts, allocates outputs with PyTorch and passes raw pointers and the current
+CUDA stream.  There is no CPU fallback: if the library is missing, every call raises.
+
+Layout: matrices are column-major.  A torch tensor ``X`` of shape (m, n) is column-major when
+``X.stride(0) == 1`` (e.g. ``A.t()`` of a contiguous (n, m) tensor); its leading dimension is
+``X.stride(1)``.  Outputs are returned as column-major views with the same convention.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import buildlib as _build
+
+_I64, _DBL, _PTR = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
+TOL_MODES = {"maxcol_abs": 0, "maxcol_rel": 1, "fro_rel": 2}
+STOP_REASONS = {0: "none", 1: "tol", 2: "break", 3: "d_max"}
+RANK_FLOOR = 1e-12
+
+
+class RbdError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int64), ("next_pivot", ctypes.c_int64), ("stop_reason", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("err_last", ctypes.c_double), ("fro_last", ctypes.c_double),
+                ("x_fro", ctypes.c_double), ("x_maxcol", ctypes.c_double)]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("pass_launches", ctypes.c_int64), ("pass_ms", ctypes.c_double),
+                ("orth_launches", ctypes.c_int64), ("orth_ms", ctypes.c_double), ("init_ms", ctypes.c_double),
+                ("pass_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load librbd.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"librbd.so not found at {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    lib.rbd_compress_workspace_bytes.restype = ctypes.c_size_t
+    lib.rbd_compress_workspace_bytes.argtypes = [_I64, _I64, _I64, ctypes.c_int]
+    lib.rbd_compress.restype = ctypes.c_int
+    lib.rbd_compress.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
+                                 _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.c_size_t, _PTR,
+                                 ctypes.POINTER(_Result)]
+    lib.rbd_compress_host.restype = ctypes.c_int
+    lib.rbd_compress_host.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
+                                      _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.POINTER(_Result)]
+    lib.rbd_project.restype = ctypes.c_int
+    lib.rbd_project.argtypes = [_PTR, _I64, _I64, _I64, _PTR, ctypes.c_int, _I64, _I64, _PTR, _I64, _PTR]
+    lib.rbd_set_profiling.restype = None
+    lib.rbd_set_profiling.argtypes = [ctypes.c_int]
+    lib.rbd_get_profile.restype = ctypes.c_int
+    lib.rbd_get_profile.argtypes = [ctypes.POINTER(_Profile)]
+    lib.rbd_status_string.restype = ctypes.c_char_p
+    lib.rbd_status_string.argtypes = [ctypes.c_int]
+    lib.rbd_version.restype = ctypes.c_int
+    lib.rbd_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().rbd_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise RbdError(status, what)
+
+
+def _colmajor(x: torch.Tensor, name: str) -> int:
+    if x.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D (rows x columns) tensor")
+    m, n = x.shape
+    if x.stride(0) != 1 and m > 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1); use t().contiguous().t()")
+    if n <= 1:
+        return max(m, 1)
+    if x.stride(1) < m:
+        raise ValueError(f"{name}: leading dimension {x.stride(1)} < rows {m}")
+    return x.stride(1)
+
+
+def _stream_ptr(device: torch.device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def colmajor_empty(m: int, n: int, dtype, device) -> torch.Tensor:
+    """Uninitialised column-major (m x n) tensor (leading dimension m)."""
+    return torch.empty((n, m), dtype=dtype, device=device).t()
+
+
+def as_colmajor(x: torch.Tensor) -> torch.Tensor:
+    """Column-major copy (or view) of a 2-D tensor."""
+    return x if x.stride(0) == 1 else x.t().contiguous().t()
+
+
+@dataclass
+class Compressed:
+    Y: torch.Tensor        # m x d, column-major, orthonormal columns
+    T: torch.Tensor        # d x n, column-major
+    pivots: torch.Tensor   # d int64
+    err: torch.Tensor      # d FP64, E_cur after each basis
+    nu: torch.Tensor       # d FP64, orthogonalised norm of each pivot
+    d: int
+    next_pivot: int
+    stop_reason: str
+    err_last: float
+    fro_last: float
+    x_fro: float
+    x_maxcol: float
+    launches: int
+
+
+def workspace_bytes(m: int, n: int, d_max: int, dtype=torch.float64) -> int:
+    return int(load().rbd_compress_workspace_bytes(m, n, d_max, DTYPES[dtype]))
+
+
+def compress(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: str = "maxcol_abs",
+             workspace: Optional[torch.Tensor] = None) -> Compressed:
+    """Algorithm 1 on a column-major CUDA tensor X (m x n) of dtype float64/float32/bfloat16."""
+    lib = load()
+    if not X.is_cuda:
+        raise ValueError("X must be a CUDA tensor (use compress_host for host arrays)")
+    if X.dtype not in DTYPES:
+        raise ValueError(f"unsupported dtype {X.dtype}")
+    m, n = X.shape
+    ldx = _colmajor(X, "X")
+    dev = X.device
+    Y = colmajor_empty(m, d_max, torch.float64, dev)
+    T = colmajor_empty(d_max, n, torch.float64, dev)
+    piv = torch.empty(d_max, dtype=torch.int64, device=dev)
+    err = torch.empty(d_max, dtype=torch.float64, device=dev)
+    nu = torch.empty(d_max, dtype=torch.float64, device=dev)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    res = _Result()
+    with torch.cuda.device(dev):
+        st = lib.rbd_compress(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, float(tol), TOL_MODES[tol_mode],
+                              int(d_max), int(start), Y.data_ptr(), m, T.data_ptr(), d_max, piv.data_ptr(),
+                              err.data_ptr(), nu.data_ptr(), ws_ptr, ws_bytes, _stream_ptr(dev),
+                              ctypes.byref(res))
+    _check(st, "rbd_compress")
+    d = int(res.d)
+    return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
+                      STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),
+                      float(res.x_fro), float(res.x_maxcol), int(res.launches))
+
+
+def compress_host(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: str = "maxcol_abs",
+                  device: Optional[torch.device] = None, out: Optional[dict] = None) -> Compressed:
+    """rbd_compress_host on a column-major CPU tensor (pinned memory makes the copies DMA).
+    ``out`` may hold preallocated (pinned) CPU outputs Y, T, pivots, err, nu."""
+    lib = load()
+    if X.is_cuda:
+        raise ValueError("compress_host takes a CPU tensor")
+    m, n = X.shape
+    ldx = _colmajor(X, "X")
+    if out is None:
+        out = {"Y": colmajor_empty(m, d_max, torch.float64, "cpu"),
+               "T": colmajor_empty(d_max, n, torch.float64, "cpu"),
+               "pivots": torch.empty(d_max, dtype=torch.int64), "err": torch.empty(d_max, dtype=torch.float64),
+               "nu": torch.empty(d_max, dtype=torch.float64)}
+    Y, T, piv, err, nu = out["Y"], out["T"], out["pivots"], out["err"], out["nu"]
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    res = _Result()
+    with torch.cuda.device(dev):
+        st = lib.rbd_compress_host(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, float(tol), TOL_MODES[tol_mode],
+                                   int(d_max), int(start), Y.data_ptr(), Y.stride(1), T.data_ptr(), T.stride(1),
+                                   piv.data_ptr(), err.data_ptr(), nu.data_ptr(), _stream_ptr(dev),
+                                   ctypes.byref(res))
+    _check(st, "rbd_compress_host")
+    d = int(res.d)
+    return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
+                      STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),
+                      float(res.x_fro), float(res.x_maxcol), int(res.launches))
+
+
+def project(Y: torch.Tensor, V: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Out-of-sample map C = Y' V (Section 3.1) for column-major CUDA tensors Y (m x d, FP64)
+    and V (m x k)."""
+    lib = load()
+    if Y.dtype != torch.float64 or not Y.is_cuda or not V.is_cuda:
+        raise ValueError("Y must be a CUDA float64 tensor and V a CUDA tensor")
+    if V.dim() == 1:
+        V = V[:, None]
+    m, d = Y.shape
+    if V.shape[0] != m:
+        raise ValueError("Y and V must have the same number of rows")
+    k = V.shape[1]
+    ldy = _colmajor(Y, "Y")
+    ldv = _colmajor(V, "V")
+    C = colmajor_empty(d, k, torch.float64, Y.device) if out is None else out
+    ldc = _colmajor(C, "out") if d > 0 and k > 0 else max(d, 1)
+    with torch.cuda.device(Y.device):
+        st = lib.rbd_project(Y.data_ptr(), m, d, ldy, V.data_ptr(), DTYPES[V.dtype], k, ldv, C.data_ptr(),
+                             ldc, _stream_ptr(Y.device))
+    _check(st, "rbd_project")
+    return C
+
+
+def set_profiling(enabled: bool):
+    load().rbd_set_profiling(1 if enabled else 0)
+
+
+def get_profile() -> dict:
+    p = _Profile()
+    _check(load().rbd_get_profile(ctypes.byref(p)), "rbd_get_profile")
+    return {f: getattr(p, f) for f, _ in _Profile._fields_}
+
+
+def version() -> int:
+    return int(load().rbd_version())

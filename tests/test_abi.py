@@ -1,0 +1,99 @@
+"""The C-ABI library: it builds, loads and exports every entry point include/rbd.h declares;
+argument validation returns status codes without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1503_05947_gb300 as rbd
+from paper_1503_05947_gb300 import rbd as rbd_binding
+from paper_1503_05947_gb300 import buildlib as pkg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rbd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(rbd_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return rbd.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("rbd_compress", "rbd_compress_host", "rbd_project", "rbd_compress_workspace_bytes",
+              "rbd_status_string", "rbd_version", "rbd_set_profiling", "rbd_get_profile"):
+        assert f in names, f
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"librbd.so does not export {name}"
+
+
+def test_library_is_built_for_sm103a(lib):
+    # the build passes exactly one -gencode for sm_103a
+    assert pkg_build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(pkg_build.LIB)
+
+
+def test_status_strings(lib):
+    assert rbd.status_string(0) == "ok"
+    assert "NaN" in rbd.status_string(4)
+    assert rbd.version() >= 100
+
+
+def test_workspace_bytes(lib):
+    assert lib.rbd_compress_workspace_bytes(0, 5, 1, 0) == 0
+    assert lib.rbd_compress_workspace_bytes(5, 5, 6, 0) == 0
+    small = lib.rbd_compress_workspace_bytes(1024, 512, 64, 0)
+    f32 = lib.rbd_compress_workspace_bytes(1024, 512, 64, 1)
+    # FP64 input keeps two FP32 planes (8 bytes/element), FP32 one plane
+    assert small >= 1024 * 512 * 8 and f32 >= 1024 * 512 * 4 and small > f32
+    assert lib.rbd_compress_workspace_bytes(8192, 8192, 512, 0) >= 8192 * 8192 * 8
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(lib):
+    P = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    res = rbd_binding._Result()
+
+    def call(**kw):
+        a = dict(X=P, xt=0, m=8, n=6, ldx=8, tol=0.0, mode=0, d_max=4, start=0, Y=P, ldy=8, T=P, ldt=4,
+                 piv=P, err=P)
+        a.update(kw)
+        return lib.rbd_compress(a["X"], a["xt"], a["m"], a["n"], a["ldx"], a["tol"], a["mode"], a["d_max"],
+                                a["start"], a["Y"], a["ldy"], a["T"], a["ldt"], a["piv"], a["err"], None, None, 0,
+                                None, ctypes.byref(res))
+
+    assert call(X=None) == 1
+    assert call(m=0) == 1
+    assert call(ldx=7) == 1
+    assert call(d_max=7) == 1          # d_max > min(m, n)
+    assert call(d_max=0) == 1
+    assert call(start=6) == 1
+    assert call(start=-1) == 1
+    assert call(tol=-1.0) == 1
+    assert call(tol=float("nan")) == 1
+    assert call(mode=3) == 1
+    assert call(xt=7) == 1
+    assert call(ldt=3) == 1
+    assert lib.rbd_project(P, 0, 2, 1, P, 0, 1, 1, P, 2, None) == 1
+    assert lib.rbd_project(P, 4, 2, 3, P, 0, 1, 4, P, 2, None) == 1   # ldy < m
+    assert lib.rbd_project(P, 4, 0, 4, P, 0, 1, 4, P, 1, None) == 0   # d = 0: no-op
+
+
+def test_no_cpu_fallback_in_product_path():
+    """The product package never imports the oracle (test infrastructure) or numpy math of
+    the method; its only compute entry points go through librbd.so."""
+    pkg = os.path.join(ROOT, "paper_1503_05947_gb300")
+    for fn in os.listdir(pkg):
+        if fn.endswith(".py"):
+            txt = open(os.path.join(pkg, fn)).read()
+            assert "import oracle" not in txt and "from oracle" not in txt, fn

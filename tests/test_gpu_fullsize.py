@@ -1,0 +1,88 @@
+"""The benchmarked workload at full size: the 8192 x 8192 quantised image-like field, FP64,
+d_max = 512, tol = 1e-3 relative Frobenius, in the launch configuration bench.py times.
+
+The oracle runs the first steps of Algorithm 1 on the full matrix (identical pivots, Y, T and
+indicators within 1e-10); the complete run is checked through properties that hold at any size:
+orthonormal Y, T(:, j) = Y' x_j on sampled columns (oracle projection), the certified
+indicator equal to the recomputed residual of the next pivot, a non-increasing indicator, and
+the Frobenius residual of the final decomposition.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gen
+from gpu_util import to_device, to_numpy
+
+pytestmark = pytest.mark.gpu
+
+N = 8192
+D_MAX = 512
+TOL = 1e-3
+ORACLE_STEPS = 6
+
+
+@pytest.fixture(scope="module")
+def workload():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    q = gen.image_like_u8(N, seed=1)
+    X = gen.u8_to_unit_f64(q)
+    return X
+
+
+@pytest.fixture(scope="module")
+def run(workload):
+    import paper_1503_05947_gb300 as rbd
+    Xd = to_device(workload)
+    r = rbd.compress(Xd, TOL, D_MAX, tol_mode="fro_rel")
+    torch.cuda.synchronize()
+    return Xd, r
+
+
+def test_first_steps_match_oracle(oracle_mod, workload, run):
+    X = workload
+    _, r = run
+    ref = oracle_mod.compress(X, 0.0, ORACLE_STEPS)
+    scale = np.linalg.norm(X, axis=0)
+    k = ORACLE_STEPS
+    assert np.array_equal(r.pivots[:k].cpu().numpy(), ref["pivots"])
+    Y = to_numpy(r.Y[:, :k])
+    T = to_numpy(r.T[:k, :])
+    assert np.linalg.norm(Y - ref["Y"], axis=0).max() <= 1e-10
+    assert (np.abs(T - ref["T"]) / scale[None, :]).max() <= 1e-10
+    assert np.abs(r.err[:k].cpu().numpy() - ref["err"]).max() <= 1e-10 * scale.max()
+    assert np.abs(r.nu[:k].cpu().numpy() - ref["nu"]).max() <= 1e-10 * scale.max()
+
+
+def test_full_run_properties(oracle_mod, workload, run):
+    X = workload
+    Xd, r = run
+    d = r.d
+    assert d == D_MAX or r.stop_reason in ("tol", "break")
+    Y = r.Y
+    G = Y.t() @ Y
+    dev = (G - torch.eye(d, dtype=torch.float64, device=G.device)).abs().max().item()
+    assert dev <= 1e-13, f"|Y'Y - I| = {dev:.3e}"
+    rng = np.random.default_rng(0)
+    cols = rng.choice(N, 48, replace=False)
+    Yc = to_numpy(Y)
+    Tp = oracle_mod.project(Yc, X[:, cols])
+    Tg = to_numpy(r.T[:, cols])
+    scale = np.linalg.norm(X[:, cols], axis=0)
+    assert (np.abs(Tg - Tp) / scale[None, :]).max() <= 1e-10
+    err = r.err.cpu().numpy()
+    nu = r.nu.cpu().numpy()
+    smax = np.linalg.norm(X, axis=0).max()
+    assert np.all(np.diff(err) <= 1e-12 * smax), "indicator increased"
+    assert np.all(np.abs(nu[1:] - err[:-1]) <= 1e-12 * smax), "certified indicator != next pivot residual"
+    # Frobenius residual of the final decomposition (FP64 GEMM on the device, in column blocks)
+    fro2 = 0.0
+    for c0 in range(0, N, 1024):
+        R = Xd[:, c0:c0 + 1024] - Y @ r.T[:, c0:c0 + 1024]
+        fro2 += float((R * R).sum())
+    fro = np.sqrt(fro2)
+    assert abs(fro - r.fro_last) <= 1e-8 * r.x_fro, (fro, r.fro_last)
+    # sampled columns' residuals never exceed the certified indicator
+    Rs = X[:, cols] - Yc @ Tg
+    assert np.linalg.norm(Rs, axis=0).max() <= err[-1] * (1 + 1e-12)
