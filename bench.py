@@ -1,0 +1,350 @@
+"""Benchmark: Reduced Basis Decomposition of the 8192 x 8192 image-like FP64 matrix on GB300.
+
+One step = one complete rbd_compress (Algorithm 1 to tolerance: the initial norm pass, then per
+basis the orthogonalisation and the fused pass over X) followed by the out-of-sample map of 64
+vectors (rbd_project).  Metric: GB/s of X streamed by the compression, i.e.
+(passes over X) * m * n * 8 bytes / step time, passes = d + 1 (the initial pass and one per
+basis), reported against the measured HBM bandwidth.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun) runs N independent replicas, one per GPU ("replicas only": one matrix does not
+shard in this build), value = total bytes of all ranks / max over ranks of the timed region.
+--impl reference times the FP64 CPU oracle (the plain implementation of Algorithm 1) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M = N = 8192
+D_MAX = 512
+TOL = 1e-3
+TOL_MODE = "fro_rel"
+N_OOS = 64
+METRIC = "RBD compress GB/s of X to tol (HBM % of peak); mixed/batched vs FP64 speedup"
+UNIT = "GB/s"
+WORKLOAD = ("image-like 8192x8192 field (200 Gaussian bumps + 20 sinusoids, uint8-quantised, /255) "
+            "in FP64; d_max=512, tol=1e-3 relative Frobenius, start column 0; + projection of 64 "
+            "out-of-sample vectors")
+PASS_SOURCES = ["paper_1503_05947_gb300/csrc/rbd_pass.cu", "paper_1503_05947_gb300/csrc/rbd_device.cuh",
+                "paper_1503_05947_gb300/csrc/rbd_work.h"]
+
+
+def pass_kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in PASS_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def ncu_traffic() -> dict | None:
+    """DRAM bytes per pass-kernel launch from the committed ncu summary, if it was taken on
+    the current pass-kernel source."""
+    p = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != pass_kernel_hash():
+        return None
+    return d
+
+
+def make_inputs(device):
+    import torch
+
+    import gen
+    q = gen.image_like_u8(M, seed=1)
+    qt = torch.from_numpy(np.ascontiguousarray(q.T))  # (n, m) row-major == column-major X
+    X = (qt.to(device=device, dtype=torch.float64) / 255.0).t()
+    V = gen.out_of_sample(M, N_OOS, seed=11)
+    Vd = torch.from_numpy(np.ascontiguousarray(V.T)).to(device).t()
+    return q, X, Vd
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier_max(world: int, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_sample(X64: np.ndarray, steps: int) -> tuple[float, float]:
+    """Time the FP64 CPU oracle on the first `steps` bases of Algorithm 1 for this matrix.
+    Returns (seconds, bytes of X the sample represents = steps * m * n * 8)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.compress(X64, 0.0, steps)
+    dt = time.perf_counter() - t0
+    assert r["d"] == steps
+    return dt, steps * X64.shape[0] * X64.shape[1] * 8.0
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the oracle on the host cores, on bounded samples of the workload."""
+    if rank != 0:
+        return
+    import gen
+    q = gen.image_like_u8(M, seed=1)
+    X64 = gen.u8_to_unit_f64(q)
+    steps_per_sample = args.ref_steps
+    for _ in range(args.warmup):
+        oracle_sample(X64, steps_per_sample)
+    times, nbytes = [], 0.0
+    for _ in range(args.steps):
+        dt, b = oracle_sample(X64, steps_per_sample)
+        times.append(dt)
+        nbytes += b
+    total = sum(times)
+    value = nbytes / total / 1e9
+    sample = (f"first {steps_per_sample} bases of Algorithm 1 on the full 8192x8192 matrix per step "
+              f"(oracle: explicit FP64 residual, MGS twice), single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "m": M, "n": N, "d_max": D_MAX, "tol": TOL,
+                                            "tol_mode": TOL_MODE, "sample_bases": steps_per_sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import paper_1503_05947_gb300 as rbd
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    rbd.load()
+    q, X, V = make_inputs(dev)
+    stream = torch.cuda.current_stream(dev)
+    ws = torch.empty(rbd.workspace_bytes(M, N, D_MAX), dtype=torch.uint8, device=dev)
+
+    def step():
+        r = rbd.compress(X, TOL, D_MAX, tol_mode=TOL_MODE, workspace=ws)
+        C = rbd.project(r.Y, V)
+        return r, C
+
+    for _ in range(args.warmup):
+        r, _ = step()
+    torch.cuda.synchronize(dev)
+
+    rbd.set_profiling(True)
+    pass_ms, pass_n, orth_ms, init_ms = 0.0, 0, 0.0, 0.0
+    passes_total = 0
+    launches = 0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            r, C = step()
+            pf = rbd.get_profile()
+            pass_ms += pf["pass_ms"]
+            pass_n += pf["pass_launches"]
+            orth_ms += pf["orth_ms"]
+            init_ms += pf["init_ms"]
+            passes_total += r.d + 1
+            launches += r.launches + 1
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    rbd.set_profiling(False)
+    t_local = e0.elapsed_time(e1) / 1e3
+    t = barrier_max(world, t_local)
+    bytes_per_pass = M * N * 8.0
+    value = world * passes_total * bytes_per_pass / t / 1e9
+
+    # end to end through the host-buffer entry point (pinned host X, copies inside the region)
+    Xh = torch.from_numpy(np.ascontiguousarray(q.T)).to(torch.float64).div_(255.0).pin_memory().t()
+    outs = {"Y": torch.empty((D_MAX, M), dtype=torch.float64).pin_memory().t(),
+            "T": torch.empty((N, D_MAX), dtype=torch.float64).pin_memory().t(),
+            "pivots": torch.empty(D_MAX, dtype=torch.int64).pin_memory(),
+            "err": torch.empty(D_MAX, dtype=torch.float64).pin_memory(),
+            "nu": torch.empty(D_MAX, dtype=torch.float64).pin_memory()}
+    rh = rbd.compress_host(Xh, TOL, D_MAX, tol_mode=TOL_MODE, device=dev, out=outs)  # warm-up
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e2e_passes = 0
+    for _ in range(e2e_steps):
+        rh = rbd.compress_host(Xh, TOL, D_MAX, tol_mode=TOL_MODE, device=dev, out=outs)
+        e2e_passes += rh.d + 1
+    t_e2e = barrier_max(world, time.perf_counter() - t0)
+    e2e_value = world * e2e_passes * bytes_per_pass / t_e2e / 1e9
+    d2h = M * rh.d * 8 + rh.d * N * 8 + rh.d * 8 * 3
+
+    peaks = measured_peaks()
+    avg_pass = pass_ms / max(pass_n, 1) / 1e3
+    achieved = bytes_per_pass / avg_pass / 1e9 if pass_n else None
+    tr = ncu_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "kernel": "rbd::pass_kernel<2> (fused pass, FP64 data as float-float planes)",
+            "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_per_pass}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        X64 = gen_x64(q)
+        dt, b = oracle_sample(X64, args.cpu_steps)
+        cpu = {"value": b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_steps} bases of Algorithm 1 on the full matrix, single thread "
+                         f"({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "m": M, "n": N, "d_max": D_MAX, "tol": TOL, "tol_mode": TOL_MODE,
+                           "bases": r.d, "passes_per_step": r.d + 1, "stop_reason": r.stop_reason,
+                           "fro_rel_residual": r.fro_last / r.x_fro, "oos_vectors": N_OOS,
+                           "l2": "inputs larger than L2 (X 512 MiB vs 129 MB L2)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": M * N * 8,
+                        "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                "gpu_launches": launches,
+                "breakdown_ms_per_step": {"pass": pass_ms / args.steps, "orth": orth_ms / args.steps,
+                                          "init": init_ms / args.steps, "pass_avg_us": avg_pass * 1e6},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
+def gen_x64(q):
+    import gen
+    return gen.u8_to_unit_f64(q)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=12, help="bases in the oracle CPU-baseline sample")
+    ap.add_argument("--ref-steps", type=int, default=3, help="bases per step of the reference arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

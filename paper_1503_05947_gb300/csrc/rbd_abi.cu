@@ -27,7 +27,8 @@ static const int kLookahead = 4;
 // ---------------------------------------------------------------------------------------
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms) {
+bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms,
+               int pass_ctas_per_sm) {
     w = Work{};
     w.m = m;
     w.n = n;
@@ -51,7 +52,9 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     w.NT = ceil_div(w.ldp, w.MT);
     w.ngroups = ceil_div(n, w.C);
     w.W = w.NT * w.ngroups;
-    w.G = (int)std::min<int64_t>(num_sms, w.W);
+    w.group_stride = (int64_t)w.C * w.planes_n * w.ldp;
+    w.tile_stride = (int64_t)w.C * w.planes_n * w.MT;
+    w.G = (int)std::min<int64_t>((int64_t)num_sms * std::max(1, pass_ctas_per_sm), w.W);
     // Largest number of CTAs sharing one column group.
     int64_t kmax = 1;
     const int64_t G = w.G, W = w.W;
@@ -81,11 +84,12 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     size_t o_lb = take((size_t)ceil_div(d_max, 8) * 4);
     size_t o_gc = take((size_t)w.ngroups * 4);
     w.zero_bytes = off;
-    size_t o_planes = take((size_t)w.planes_n * ldp * (size_t)n * w.esize);
+    size_t o_planes = take((size_t)w.ngroups * (size_t)w.group_stride * w.esize);
     size_t o_yh = take(ldp * (size_t)d_max * 4);
     size_t o_yl = take(ldp * (size_t)d_max * 4);
     size_t o_v1 = take(ldp * 8), o_v2 = take(ldp * 8);
-    size_t o_v1h = take(ldp * 4), o_v1l = take(ldp * 4), o_v2h = take(ldp * 4), o_v2l = take(ldp * 4);
+    size_t o_v1h = take(ldp * 4), o_v1l = take(ldp * 4);
+    size_t o_v2s = take((size_t)w.NT * 2 * w.MT * 4);
     size_t o_e = take((size_t)n * 8), o_xn2 = take((size_t)n * 8);
     size_t o_vpart = take((size_t)w.LC_MAX * ldp * 8);
     size_t o_hpart = take((size_t)w.RC_MAX * (size_t)d_max * 8);
@@ -107,8 +111,7 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     w.v2 = (double*)o_v2;
     w.v1h = (float*)o_v1h;
     w.v1l = (float*)o_v1l;
-    w.v2h = (float*)o_v2h;
-    w.v2l = (float*)o_v2l;
+    w.v2s = (float*)o_v2s;
     w.e = (double*)o_e;
     w.xn2 = (double*)o_xn2;
     w.vpart = (double*)o_vpart;
@@ -137,8 +140,7 @@ void carve_work(Work& w, void* base) {
     RB_REBASE(v2);
     RB_REBASE(v1h);
     RB_REBASE(v1l);
-    RB_REBASE(v2h);
-    RB_REBASE(v2l);
+    RB_REBASE(v2s);
     RB_REBASE(e);
     RB_REBASE(xn2);
     RB_REBASE(vpart);
@@ -157,12 +159,13 @@ void carve_work(Work& w, void* base) {
 // ---------------------------------------------------------------------------------------
 struct DeviceState {
     int num_sms = 0;
+    int pass_ctas_per_sm[3] = {1, 1, 1};
     bool ready = false;
 };
 static std::mutex g_dev_mu;
 static DeviceState g_dev[64];
 
-static cudaError_t device_state(int& num_sms) {
+static cudaError_t device_state(int& num_sms, int* ctas_per_sm = nullptr) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -172,11 +175,13 @@ static cudaError_t device_state(int& num_sms) {
     if (!s.ready) {
         e = cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = pass_kernel_setup();
+        e = pass_kernel_setup(s.pass_ctas_per_sm);
         if (e != cudaSuccess) return e;
         s.ready = true;
     }
     num_sms = s.num_sms;
+    if (ctas_per_sm)
+        for (int i = 0; i < 3; ++i) ctas_per_sm[i] = s.pass_ctas_per_sm[i];
     return cudaSuccess;
 }
 
@@ -250,11 +255,11 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
                                   double* T, int64_t ldt, int64_t* pivots, double* err, double* nu,
                                   void* workspace, size_t workspace_bytes, cudaStream_t st,
                                   rbd_result* result) {
-    int num_sms = 0;
-    cudaError_t ce = device_state(num_sms);
+    int num_sms = 0, occ[3] = {1, 1, 1};
+    cudaError_t ce = device_state(num_sms, occ);
     if (ce != cudaSuccess) return map_cuda(ce);
     Work w;
-    if (!plan_work(w, m, n, ldx, d_max, (int)xt, num_sms)) return RBD_EUNSUPPORTED;
+    if (!plan_work(w, m, n, ldx, d_max, (int)xt, num_sms, occ[(int)xt])) return RBD_EUNSUPPORTED;
     if (xt == RBD_BF16) return RBD_EUNSUPPORTED;
 
     bool own = false;
@@ -443,13 +448,13 @@ extern "C" {
 
 size_t rbd_compress_workspace_bytes(int64_t m, int64_t n, int64_t d_max, rbd_dtype xt) {
     if (m < 1 || n < 1 || d_max < 1 || d_max > m || d_max > n || !valid_dtype((int)xt)) return 0;
-    int num_sms = 0;
-    if (device_state(num_sms) != cudaSuccess) {
+    int num_sms = 0, occ[3] = {RBD_PASS_MINB, RBD_PASS_MINB, 1};
+    if (device_state(num_sms, occ) != cudaSuccess) {
         cudaGetLastError();
         num_sms = 160;  // upper bound for planning without a device
     }
     Work w;
-    if (!plan_work(w, m, n, m, d_max, (int)xt, num_sms)) return 0;
+    if (!plan_work(w, m, n, m, d_max, (int)xt, num_sms, occ[(int)xt])) return 0;
     return w.total_bytes;
 }
 

@@ -101,6 +101,24 @@ __device__ __forceinline__ double ff_to_double(float s, float c) {
     return (double)s + (double)c;
 }
 
+// (s, c) += (s2, c2): the leading parts are added exactly (TwoSum), the compensations in FP32.
+__device__ __forceinline__ void ff_add(float& s, float& c, float s2, float c2) {
+    float t, e;
+    two_sum(s, s2, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(c2, e));
+}
+
+// Float-float sum over the 32 lanes of a warp (fixed tree); the result is valid in lane 0.
+__device__ __forceinline__ void warp_sum_ff(float& s, float& c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+        ff_add(s, c, s2, c2);
+    }
+}
+
 // x ~= hi + lo with |x - hi - lo| <= 2^-48 |x| (for |x| in the FP32 normal range).
 __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
     hi = __double2float_rn(x);

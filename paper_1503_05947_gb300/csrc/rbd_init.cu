@@ -1,7 +1,7 @@
 // rbd_init.cu -- the initial pass over X (Section 3.3, "pre-computation of diag(X'AX)" with
 // A = I): e_j = ||X(:, j)||^2 for every column, ||X||_F and max_j ||X(:, j)|| for the
-// tolerance modes, and the one-time re-layout of X into the padded plane format the fused
-// pass streams with bulk copies (see rbd_work.h).
+// tolerance modes, and the one-time re-layout of X into the tile-major plane format the fused
+// pass streams with bulk copies (rbd_work.h).
 #include "rbd_device.cuh"
 #include "rbd_work.h"
 
@@ -10,6 +10,9 @@ namespace rbd {
 struct InitParams {
     const void* X;
     int64_t ldx, m, n, ldp;
+    int64_t ncols_pad;        // ngroups * C: columns of the plane layout
+    int C, MT;
+    int64_t group_stride, tile_stride;
     void* planes;
     double* e;
     double* xn2;
@@ -40,63 +43,74 @@ __device__ __forceinline__ void split_f64_fast(double x, float& hi, float& lo) {
     }
 }
 
+// One warp per column of the plane layout; lane l handles rows 4l..4l+3 of every 128-row chunk.
 template <int XT>
 __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
+    constexpr int P = (XT == 0) ? 2 : 1;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int bad = ST_OK;
-    for (int64_t j = gw; j < p.n; j += nw) {
-        float s = 0.f, c = 0.f;
-        if (XT == 0) {  // FP64 -> two FP32 planes
-            const double* xj = (const double*)p.X + j * p.ldx;
-            float* ph = (float*)p.planes + j * p.ldp;
-            float* pl = (float*)p.planes + (p.n + j) * p.ldp;
-            for (int64_t r = lane; r < p.ldp; r += 32) {
-                const double x = (r < p.m) ? xj[r] : 0.0;
-                float hi, lo;
-                if (!isfinite(x)) {
-                    bad = ST_ENONFINITE;
-                    hi = lo = 0.f;
-                } else {
-                    if (fabs(x) >= 0x1p127) bad = (bad == ST_OK) ? ST_EUNSUPPORTED : bad;
-                    split_f64_fast(x, hi, lo);
+    for (int64_t j = gw; j < p.ncols_pad; j += nw) {
+        const int64_t g = j / p.C;
+        const int c = (int)(j % p.C);
+        const bool live = j < p.n;
+        float s = 0.f, cc = 0.f;
+        for (int64_t r0 = 4 * lane; r0 < p.ldp; r0 += 128) {
+            const int64_t t = r0 / p.MT;
+            const int64_t rt = min((int64_t)p.MT, p.ldp - t * p.MT);
+            const int64_t base = g * p.group_stride + t * p.tile_stride + (int64_t)c * P * rt + (r0 - t * p.MT);
+            double x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t r = r0 + q;
+                x[q] = 0.0;
+                if (live && r < p.m) {
+                    if (XT == 0) x[q] = ((const double*)p.X)[j * p.ldx + r];
+                    else if (XT == 1) x[q] = (double)((const float*)p.X)[j * p.ldx + r];
+                    else x[q] = (double)__bfloat162float(((const __nv_bfloat16*)p.X)[j * p.ldx + r]);
                 }
-                ph[r] = hi;
-                pl[r] = lo;
-                ff_mac2(s, c, hi, lo, hi, lo);
+                if (!isfinite(x[q])) {
+                    bad = ST_ENONFINITE;
+                    x[q] = 0.0;
+                }
             }
-        } else if (XT == 1) {  // FP32 -> one FP32 plane
-            const float* xj = (const float*)p.X + j * p.ldx;
-            float* ph = (float*)p.planes + j * p.ldp;
-            for (int64_t r = lane; r < p.ldp; r += 32) {
-                float x = (r < p.m) ? xj[r] : 0.f;
-                if (!isfinite(x)) {
-                    bad = ST_ENONFINITE;
-                    x = 0.f;
+            if (XT == 0) {
+                float hi[4], lo[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (fabs(x[q]) >= 0x1p127) bad = (bad == ST_OK) ? ST_EUNSUPPORTED : bad;
+                    split_f64_fast(x[q], hi[q], lo[q]);
+                    ff_mac2(s, cc, hi[q], lo[q], hi[q], lo[q]);
                 }
-                ph[r] = x;
-                ff_mac1(s, c, x, x, 0.f);
-            }
-        } else {  // BF16 -> one BF16 plane
-            const __nv_bfloat16* xj = (const __nv_bfloat16*)p.X + j * p.ldx;
-            __nv_bfloat16* ph = (__nv_bfloat16*)p.planes + j * p.ldp;
-            for (int64_t r = lane; r < p.ldp; r += 32) {
-                __nv_bfloat16 xb = (r < p.m) ? xj[r] : __float2bfloat16(0.f);
-                float x = __bfloat162float(xb);
-                if (!isfinite(x)) {
-                    bad = ST_ENONFINITE;
-                    x = 0.f;
-                    xb = __float2bfloat16(0.f);
+                float* ph = (float*)p.planes + base;
+                *reinterpret_cast<float4*>(ph) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<float4*>(ph + rt) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            } else if (XT == 1) {
+                float v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v[q] = (float)x[q];
+                    ff_mac1(s, cc, v[q], v[q], 0.f);
                 }
-                ph[r] = xb;
-                ff_mac1(s, c, x, x, 0.f);
+                *reinterpret_cast<float4*>((float*)p.planes + base) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+                __nv_bfloat16 v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v[q] = __float2bfloat16((float)x[q]);  // exact: the value came from bf16
+                    const float f = (float)x[q];
+                    ff_mac1(s, cc, f, f, 0.f);
+                }
+                __nv_bfloat162* pb = reinterpret_cast<__nv_bfloat162*>((__nv_bfloat16*)p.planes + base);
+                pb[0] = __halves2bfloat162(v[0], v[1]);
+                pb[1] = __halves2bfloat162(v[2], v[3]);
             }
         }
-        const double t = warp_sum_double(ff_to_double(s, c));
-        if (lane == 0) {
-            p.e[j] = t;
-            p.xn2[j] = t;
+        const double tsum = warp_sum_double(ff_to_double(s, cc));
+        if (live && lane == 0) {
+            p.e[j] = tsum;
+            p.xn2[j] = tsum;
         }
     }
     if (bad != ST_OK) raise_status(p.ctl, bad);
@@ -164,6 +178,11 @@ cudaError_t launch_init(const Work& w, const void* X, double tol, int mode, int6
     p.m = w.m;
     p.n = w.n;
     p.ldp = w.ldp;
+    p.ncols_pad = w.ngroups * w.C;
+    p.C = w.C;
+    p.MT = w.MT;
+    p.group_stride = w.group_stride;
+    p.tile_stride = w.tile_stride;
     p.planes = w.planes;
     p.e = w.e;
     p.xn2 = w.xn2;
@@ -172,8 +191,7 @@ cudaError_t launch_init(const Work& w, const void* X, double tol, int mode, int6
     p.mode = mode;
     p.start = start;
     p.d_max = w.d_max;
-    const int64_t warps = w.n;
-    int blocks = (int)ceil_div(warps, 8);
+    int blocks = (int)ceil_div(p.ncols_pad, 8);
     const int cap = w.num_sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;

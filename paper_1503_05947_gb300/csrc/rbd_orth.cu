@@ -51,6 +51,7 @@ struct GemvNParams {
     const double* xn2;
     uint32_t* progress;       // C: host-mapped {steps finished, stop} (may be null)
     int64_t m, ldp, k, LC, LCH, RB;
+    int64_t MT;               // C: tile rows of the tile-interleaved split output (v2s)
     Ctl* ctl;
 };
 
@@ -93,14 +94,31 @@ __global__ void __launch_bounds__(256) orth_gemv_n_kernel(GemvNParams p) {
     __syncthreads();
 
     float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t l = lbeg + ls; l < lend; l += 8) {
-        const float4 a = *(const float4*)(p.yh + l * p.ldp + r);
-        const float4 b = *(const float4*)(p.yl + l * p.ldp + r);
-        const float th = ch[l - lbeg], tl = cl[l - lbeg];
-        ff_mac2(s[0], c[0], a.x, b.x, th, tl);
-        ff_mac2(s[1], c[1], a.y, b.y, th, tl);
-        ff_mac2(s[2], c[2], a.z, b.z, th, tl);
-        ff_mac2(s[3], c[3], a.w, b.w, th, tl);
+    // batches of kU coefficients: all loads of a batch are issued before its arithmetic
+    constexpr int kU = 4;
+    for (int64_t l0 = lbeg + ls; l0 < lend; l0 += 8 * kU) {
+        float4 a[kU], b[kU];
+        float th[kU], tl[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t l = l0 + 8 * u;
+            if (l < lend) {
+                a[u] = *(const float4*)(p.yh + l * p.ldp + r);
+                b[u] = *(const float4*)(p.yl + l * p.ldp + r);
+                th[u] = ch[l - lbeg];
+                tl[u] = cl[l - lbeg];
+            } else {
+                a[u] = b[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                th[u] = tl[u] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            ff_mac2(s[0], c[0], a[u].x, b[u].x, th[u], tl[u]);
+            ff_mac2(s[1], c[1], a[u].y, b[u].y, th[u], tl[u]);
+            ff_mac2(s[2], c[2], a[u].z, b[u].z, th[u], tl[u]);
+            ff_mac2(s[3], c[3], a[u].w, b[u].w, th[u], tl[u]);
+        }
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) red[ls * kGemvRows + 4 * q + e] = ff_to_double(s[e], c[e]);
@@ -131,8 +149,17 @@ __global__ void __launch_bounds__(256) orth_gemv_n_kernel(GemvNParams p) {
         p.vout[row] = v;
         float hi, lo;
         split_double(v, hi, lo);
-        p.vouth[row] = hi;
-        p.voutl[row] = lo;
+        if (p.mode == 0) {
+            p.vouth[row] = hi;
+            p.voutl[row] = lo;
+        } else {
+            // tile-interleaved for the fused pass: tile t = [hi(rows_t) | lo(rows_t)]
+            const int64_t t = row / p.MT;
+            const int64_t rt = min(p.MT, p.ldp - t * p.MT);
+            const int64_t off = t * 2 * p.MT + (row - t * p.MT);
+            p.vouth[off] = hi;
+            p.vouth[off + rt] = lo;
+        }
     }
     if (tid == 0) p.rb_cnt[rb] = 0;
     if (p.mode == 0) return;
@@ -222,15 +249,28 @@ __global__ void __launch_bounds__(256) orth_gemv_t_kernel(GemvTParams p) {
     __shared__ int s_last;
     if (l < p.k) {
         float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int64_t r = r0 + 4 * lane; r < r1; r += 128) {
-            const float4 a = *(const float4*)(p.yh + l * p.ldp + r);
-            const float4 b = *(const float4*)(p.yl + l * p.ldp + r);
-            const float4 x = *(const float4*)(p.vh + r);
-            const float4 y = *(const float4*)(p.vl + r);
-            ff_mac2(s[0], c[0], a.x, b.x, x.x, y.x);
-            ff_mac2(s[1], c[1], a.y, b.y, x.y, y.y);
-            ff_mac2(s[2], c[2], a.z, b.z, x.z, y.z);
-            ff_mac2(s[3], c[3], a.w, b.w, x.w, y.w);
+        constexpr int kU = 4;
+        for (int64_t rr = r0 + 4 * lane; rr < r1; rr += 128 * kU) {
+            float4 a[kU], b[kU], x[kU], y[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t r = rr + 128 * u;
+                if (r < r1) {
+                    a[u] = *(const float4*)(p.yh + l * p.ldp + r);
+                    b[u] = *(const float4*)(p.yl + l * p.ldp + r);
+                    x[u] = *(const float4*)(p.vh + r);
+                    y[u] = *(const float4*)(p.vl + r);
+                } else {
+                    a[u] = b[u] = x[u] = y[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                ff_mac2(s[0], c[0], a[u].x, b[u].x, x[u].x, y[u].x);
+                ff_mac2(s[1], c[1], a[u].y, b[u].y, x[u].y, y[u].y);
+                ff_mac2(s[2], c[2], a[u].z, b[u].z, x[u].z, y[u].z);
+                ff_mac2(s[3], c[3], a[u].w, b[u].w, x[u].w, y[u].w);
+            }
         }
         double t = ff_to_double(s[0], c[0]) + ff_to_double(s[1], c[1]) + ff_to_double(s[2], c[2]) +
                    ff_to_double(s[3], c[3]);
@@ -313,8 +353,9 @@ cudaError_t launch_orth_c(const Work& w, int64_t k, int64_t* pivots, double* nu_
     p.h = w.h;
     p.vin = w.v1;
     p.vout = w.v2;
-    p.vouth = w.v2h;
-    p.voutl = w.v2l;
+    p.vouth = w.v2s;
+    p.voutl = nullptr;
+    p.MT = w.MT;
     p.nu2part = w.nu2part;
     p.pivots = pivots;
     p.nu_out = nu_out;

@@ -11,11 +11,12 @@
 // streaming pass over X per step, no m-length work per column.
 //
 // Layout and work split (GB300, 152 SMs, one persistent CTA per SM):
-//   * X lives in HBM as FP32 planes (rbd_work.h); a unit of work is a tile of MT rows x C
-//     columns.  The W = NT * ngroups units are enumerated column-group-major and split into
-//     G contiguous, equal ranges (one per CTA), so every SM streams the same number of bytes.
-//   * One producer warp moves each unit into a shared-memory ring with bulk (TMA) copies --
-//     one copy per column segment and plane plus the matching tile of the pivot vector --
+//   * X lives in HBM as tile-major FP32 planes (rbd_work.h); a unit of work is one tile of
+//     MT rows x C columns (both planes contiguous, 32 KB for FP64 input).  The
+//     W = NT * ngroups units are enumerated column-group-major and split into G contiguous,
+//     equal ranges (one per CTA), so every SM streams the same number of bytes.
+//   * One producer thread moves each unit into a shared-memory ring with two bulk (TMA)
+//     copies -- the whole X tile and the matching tile of the split pivot vector --
 //     completing on an mbarrier; X is read with an L2 evict-first policy so the split copy of
 //     Y stays cached for the orthogonalisation kernels.
 //   * Eight consumer warps each own CPW columns of the tile; lane l multiplies rows 4l..4l+3
@@ -31,9 +32,9 @@ namespace rbd {
 
 struct PassParams {
     const void* planes;
-    int64_t plane_stride;     // elements between planes (ldp * n)
-    const float* xih;         // split unnormalised pivot vector v2 (ldp)
-    const float* xil;
+    int64_t group_stride;     // elements per column group of the tile-major planes
+    int64_t tile_stride;      // elements per full row tile of a group
+    const float* xis;         // split unnormalised pivot vector v2, tile-interleaved
     const double* v2;         // FP64 v2, for Y(:, k)
     double* Y;
     int64_t ldy;
@@ -62,8 +63,44 @@ __device__ __forceinline__ int64_t unit_owner(int64_t u, int64_t W, int64_t G) {
     return ((u + 1) * G + W - 1) / W - 1;
 }
 
+// Float-float dot-product contributions of one staged tile for this warp's CPW columns.
+// Stage layout: [xi hi (rows) | xi lo (rows) | pad to 2*MT | column c plane p at (c*P + p)*rows].
+// FULL tiles (rows == MT) compile to straight-line code; the ragged last row tile of a column
+// group takes the generic path.
+template <int P, int CPW, int MT, bool FULL>
+__device__ __forceinline__ void consume_tile(const float* __restrict__ st, int rows, int warp, int lane,
+                                             float (&acc_s)[CPW][4], float (&acc_c)[CPW][4]) {
+    constexpr int XI = 2 * MT;
+    const int R = FULL ? MT : rows;
+    const int nsl = FULL ? MT / 128 : (rows >> 7);
+#pragma unroll
+    for (int sl = 0; sl < MT / 128; ++sl) {
+        if (!FULL && sl >= nsl) break;
+        const int off = sl * 128 + lane * 4;
+        const float4 zh = *reinterpret_cast<const float4*>(st + off);
+        const float4 zl = *reinterpret_cast<const float4*>(st + R + off);
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+            const float* col = st + XI + (warp * CPW + q) * P * R + off;
+            const float4 a = *reinterpret_cast<const float4*>(col);
+            if (P == 2) {
+                const float4 al = *reinterpret_cast<const float4*>(col + R);
+                ff_mac2(acc_s[q][0], acc_c[q][0], a.x, al.x, zh.x, zl.x);
+                ff_mac2(acc_s[q][1], acc_c[q][1], a.y, al.y, zh.y, zl.y);
+                ff_mac2(acc_s[q][2], acc_c[q][2], a.z, al.z, zh.z, zl.z);
+                ff_mac2(acc_s[q][3], acc_c[q][3], a.w, al.w, zh.w, zl.w);
+            } else {
+                ff_mac1(acc_s[q][0], acc_c[q][0], a.x, zh.x, zl.x);
+                ff_mac1(acc_s[q][1], acc_c[q][1], a.y, zh.y, zl.y);
+                ff_mac1(acc_s[q][2], acc_c[q][2], a.z, zh.z, zl.z);
+                ff_mac1(acc_s[q][3], acc_c[q][3], a.w, zh.w, zl.w);
+            }
+        }
+    }
+}
+
 template <int P>
-__global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) pass_kernel(PassParams p) {
+__global__ void __launch_bounds__(PassCfg<P>::THREADS, RBD_PASS_MINB) pass_kernel(PassParams p) {
     using Cfg = PassCfg<P>;
     constexpr int NW = Cfg::NW, CPW = Cfg::CPW, C = Cfg::C, MT = Cfg::MT, S = Cfg::S;
     constexpr int XI = Cfg::XI_FLOATS, STAGE = Cfg::STAGE_FLOATS;
@@ -75,8 +112,9 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) pass_kernel(PassParams
     uint64_t* empty = full + S;
     double* red_e = reinterpret_cast<double*>(empty + S);   // NW
     int64_t* red_j = reinterpret_cast<int64_t*>(red_e + NW); // NW
-    double* grp_e = reinterpret_cast<double*>(red_j + NW);   // C
-    int* flag = reinterpret_cast<int*>(grp_e + C);
+    double* grp_e = reinterpret_cast<double*>(red_j + NW);   // 2 x C (double buffer)
+    int* flag = reinterpret_cast<int*>(grp_e + 2 * C);
+    static_assert((2 * NW + 2 * C) * 8 + 16 <= (int)Cfg::SCRATCH, "scratch too small");
 
     Ctl* ctl = p.ctl;
     if (ctl->stop != 0 || ctl->status != 0) return;  // uniform: set before this launch
@@ -120,30 +158,31 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) pass_kernel(PassParams
             const uint64_t pol_x = p.evict_first ? l2_policy_evict_first() : l2_policy_evict_normal();
             const uint64_t pol_xi = l2_policy_evict_normal();
             const float* planes = static_cast<const float*>(p.planes);
+            // running (group, tile) and (stage, phase) counters: no divisions in the loop
+            int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
+            int s = 0;
+            uint32_t ph = 0;
+            bool reuse = false;
             for (int64_t u = L0; u < L1; ++u) {
-                const int64_t i = u - L0;
-                const int s = (int)(i % S);
-                const uint32_t use = (uint32_t)(i / S);
-                if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1u)) {
+                if (reuse && !mbar_wait(&empty[s], ph ^ 1u)) {
                     raise_status(ctl, ST_ETIMEOUT);
                     break;
                 }
-                const int64_t g = u / NT, t = u % NT;
-                const int64_t c0 = g * C;
-                const int ncols = (int)min((int64_t)C, p.n - c0);
-                const int64_t r0 = t * MT;
-                const int rows = (int)min((int64_t)MT, p.ldp - r0);
-                const uint32_t seg = (uint32_t)rows * 4u;
+                const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                const uint32_t xi_bytes = 2u * rows * 4u;
+                const uint32_t x_bytes = (uint32_t)(C * P) * rows * 4u;
                 float* st = stages + (size_t)s * STAGE;
-                mbar_arrive_expect_tx(&full[s], (uint32_t)(2 + ncols * P) * seg);
-                bulk_g2s(st, p.xih + r0, seg, &full[s], pol_xi);
-                bulk_g2s(st + MT, p.xil + r0, seg, &full[s], pol_xi);
-                for (int c = 0; c < ncols; ++c) {
-#pragma unroll
-                    for (int pl = 0; pl < P; ++pl) {
-                        const float* src = planes + pl * p.plane_stride + (c0 + c) * p.ldp + r0;
-                        bulk_g2s(st + XI + (c * P + pl) * MT, src, seg, &full[s], pol_x);
-                    }
+                mbar_arrive_expect_tx(&full[s], xi_bytes + x_bytes);
+                bulk_g2s(st, p.xis + t * 2 * MT, xi_bytes, &full[s], pol_xi);
+                bulk_g2s(st + XI, planes + g * p.group_stride + t * p.tile_stride, x_bytes, &full[s], pol_x);
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1u;
+                    reuse = true;
+                }
+                if (++t == NT) {
+                    t = 0;
+                    ++g;
                 }
             }
         }
@@ -159,46 +198,48 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) pass_kernel(PassParams
     double best_e = -1.0;
     int64_t best_j = INT64_MAX;
     bool ok = true;
+    double e_old[CPW];          // e_j of this warp's columns, prefetched when a group starts
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) e_old[q] = 0.0;
+    int gbuf = 0;               // double buffer of the per-group sums in shared memory
 
+    int64_t g_next = L0 / NT, t_next = L0 - (L0 / NT) * NT;
+    int s_next = 0;
+    uint32_t ph_next = 0;
     for (int64_t u = L0; u < L1; ++u) {
-        const int64_t i = u - L0;
-        const int s = (int)(i % S);
-        const uint32_t use = (uint32_t)(i / S);
-        if (ok && !mbar_wait(&full[s], use & 1u)) {
+        const int64_t g = g_next, t = t_next;
+        const int s = s_next;
+        const uint32_t ph = ph_next;
+        if (++s_next == S) {
+            s_next = 0;
+            ph_next ^= 1u;
+        }
+        if (++t_next == NT) {
+            t_next = 0;
+            ++g_next;
+        }
+        const int64_t c0 = g * C;
+        const int ncols = (int)min((int64_t)C, p.n - c0);
+        if (lane == 0 && (t == 0 || u == L0)) {
+            // the finalisation at the end of the group needs e_j: load it now, off the
+            // critical path (only the finaliser of column j writes e_j, after this read)
+#pragma unroll
+            for (int q = 0; q < CPW; ++q) {
+                const int cw = warp * CPW + q;
+                if (cw < ncols) e_old[q] = p.e[c0 + cw];
+            }
+        }
+        if (ok && !mbar_wait(&full[s], ph)) {
             raise_status(ctl, ST_ETIMEOUT);
             ok = false;
         }
-        const int64_t g = u / NT, t = u % NT;
-        const int64_t c0 = g * C;
-        const int ncols = (int)min((int64_t)C, p.n - c0);
         const int rows = (int)min((int64_t)MT, p.ldp - t * MT);
         if (ok) {
             const float* st = stages + (size_t)s * STAGE;
-            for (int sl = 0; sl < rows / 128; ++sl) {
-                const int off = sl * 128 + lane * 4;
-                const float4 zh = *reinterpret_cast<const float4*>(st + off);
-                const float4 zl = *reinterpret_cast<const float4*>(st + MT + off);
-#pragma unroll
-                for (int q = 0; q < CPW; ++q) {
-                    const int cw = warp * CPW + q;
-                    if (cw < ncols) {
-                        const float* col = st + XI + cw * P * MT + off;
-                        const float4 a = *reinterpret_cast<const float4*>(col);
-                        if (P == 2) {
-                            const float4 al = *reinterpret_cast<const float4*>(col + MT);
-                            ff_mac2(acc_s[q][0], acc_c[q][0], a.x, al.x, zh.x, zl.x);
-                            ff_mac2(acc_s[q][1], acc_c[q][1], a.y, al.y, zh.y, zl.y);
-                            ff_mac2(acc_s[q][2], acc_c[q][2], a.z, al.z, zh.z, zl.z);
-                            ff_mac2(acc_s[q][3], acc_c[q][3], a.w, al.w, zh.w, zl.w);
-                        } else {
-                            ff_mac1(acc_s[q][0], acc_c[q][0], a.x, zh.x, zl.x);
-                            ff_mac1(acc_s[q][1], acc_c[q][1], a.y, zh.y, zl.y);
-                            ff_mac1(acc_s[q][2], acc_c[q][2], a.z, zh.z, zl.z);
-                            ff_mac1(acc_s[q][3], acc_c[q][3], a.w, zh.w, zl.w);
-                        }
-                    }
-                }
-            }
+            if (rows == MT)
+                consume_tile<P, CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
+            else
+                consume_tile<P, CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -206,16 +247,18 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) pass_kernel(PassParams
         if (t != NT - 1 && u != L1 - 1) continue;
 
         // ---- end of this CTA's share of column group g: reduce and finalise ----
+        // The four accumulators and the 32 lanes are combined in float-float arithmetic on the
+        // FP32 pipe (fixed order); only lane 0 converts the result to FP64.
         double tot[CPW];
 #pragma unroll
         for (int q = 0; q < CPW; ++q) {
-            double v = 0.0;
+            float sq = acc_s[q][0], cq = acc_c[q][0];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                v += ff_to_double(acc_s[q][e], acc_c[q][e]);
-                acc_s[q][e] = acc_c[q][e] = 0.f;
-            }
-            tot[q] = warp_sum_double(v);
+            for (int e = 1; e < 4; ++e) ff_add(sq, cq, acc_s[q][e], acc_c[q][e]);
+            warp_sum_ff(sq, cq);
+            tot[q] = ff_to_double(sq, cq);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc_s[q][e] = acc_c[q][e] = 0.f;
         }
         const bool whole = (g * NT >= L0) && ((g + 1) * NT <= L1);
         if (!whole) {
@@ -258,9 +301,9 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) pass_kernel(PassParams
                     const int64_t j = c0 + cw;
                     const double cj = tot[q] * inv_nu;
                     p.T[j * p.ldt + k] = cj;
-                    const double en = (j == piv) ? 0.0 : fmax(p.e[j] - cj * cj, 0.0);
+                    const double en = (j == piv) ? 0.0 : fmax(e_old[q] - cj * cj, 0.0);
                     p.e[j] = en;
-                    grp_e[cw] = en;
+                    grp_e[gbuf * C + cw] = en;
                     if (better(en, j, best_e, best_j)) {
                         best_e = en;
                         best_j = j;
@@ -268,13 +311,15 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) pass_kernel(PassParams
                 }
             }
         }
+        // one barrier per group: thread 0 sums this buffer while the other warps move on; the
+        // buffer is written again two groups later, after thread 0 has passed the next barrier
         named_bar(1, NCONS);
         if (tid == 0) {
             double sacc = 0.0;
-            for (int cw = 0; cw < ncols; ++cw) sacc += grp_e[cw];
+            for (int cw = 0; cw < ncols; ++cw) sacc += grp_e[gbuf * C + cw];
             p.gsum[g] = sacc;
         }
-        named_bar(1, NCONS);
+        gbuf ^= 1;
     }
 
     // ---- per-CTA argmax candidate, then the grid-level last arriver ----
@@ -345,21 +390,30 @@ static cudaError_t launch_pass_p(const Work& w, PassParams& p, cudaStream_t st) 
     return cudaGetLastError();
 }
 
-cudaError_t pass_kernel_setup() {
+cudaError_t pass_kernel_setup(int ctas_per_sm[3]) {
     cudaError_t e = cudaFuncSetAttribute(pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)PassCfg<2>::SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PassCfg<1>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassCfg<1>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm[0], pass_kernel<2>, PassCfg<2>::THREADS,
+                                                          PassCfg<2>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm[1], pass_kernel<1>, PassCfg<1>::THREADS,
+                                                          PassCfg<1>::SMEM);
+    ctas_per_sm[2] = 1;
+    for (int i = 0; i < 3; ++i)
+        if (ctas_per_sm[i] < 1) ctas_per_sm[i] = 1;
+    return e;
 }
 
 cudaError_t launch_pass(const Work& w, double* Y, int64_t ldy, double* T, int64_t ldt, int64_t k,
                         uint32_t* progress, cudaStream_t st) {
     PassParams p;
     p.planes = w.planes;
-    p.plane_stride = w.ldp * w.n;
-    p.xih = w.v2h;
-    p.xil = w.v2l;
+    p.group_stride = w.group_stride;
+    p.tile_stride = w.tile_stride;
+    p.xis = w.v2s;
     p.v2 = w.v2;
     p.Y = Y;
     p.ldy = ldy;

@@ -2,12 +2,18 @@
 //
 // HBM layout (all regions 256-byte aligned, carved from one workspace allocation):
 //   ctl      control block (Ctl)
-//   planes   X re-laid out once, column-major with leading dimension ldp = round_up(m, 128),
-//            rows m..ldp-1 zero:  FP64 input -> two FP32 planes (hi, lo) with
-//            hi + lo = x to 2^-48 relative;  FP32 input -> one FP32 plane;  BF16 -> one BF16
-//            plane.  Plane p of column j starts at planes + (p * n + j) * ldp elements.
+//   planes   X re-laid out once by the initial pass, TILE-MAJOR, so that one bulk copy moves
+//            one whole work tile of the fused pass.  FP64 input -> two FP32 planes (hi, lo)
+//            with hi + lo = x to 2^-48 relative; FP32 input -> one FP32 plane; BF16 input ->
+//            one BF16 plane.  Columns are grouped by C and rows padded to ldp = round_up(m, 128)
+//            (padding rows and the padding columns of the last group are zero).  Row tiles
+//            have MT rows except the last one (rows_t = ldp - t * MT, a multiple of 128).
+//            Element (row R, column J, plane p), g = J / C, c = J % C, t = R / MT, r = R % MT:
+//                g * C * P * ldp  +  t * C * P * MT  +  (c * P + p) * rows_t  +  r
 //   yh, yl   split FP32 copy of Y (ldp x d_max each), read by the orthogonalisation GEMVs
-//   v1,v2    FP64 work vectors of the current step (ldp) and their split copies
+//   v1, v2   FP64 work vectors of the current step (ldp) and split copies:
+//            v1h/v1l plain (ldp each); v2s tile-interleaved for the pass: tile t holds
+//            [hi(rows_t) | lo(rows_t)] at offset t * 2 * MT.
 //   e, xn2   running squared residuals e_j and the initial squared norms ||x_j||^2 (n each)
 //   vpart    partial sums of the row-parallel GEMVs (LC_MAX x ldp)
 //   hpart, h partial and final re-orthogonalisation coefficients (RC_MAX x d_max, d_max)
@@ -23,33 +29,55 @@
 
 #include <cuda_runtime.h>
 
+// Fused-pass tile shape (compile-time; the defaults are the tuned GB300 values).
+#ifndef RBD_PASS_NW
+#define RBD_PASS_NW 8      // consumer warps per CTA
+#endif
+#ifndef RBD_PASS_CPW
+#define RBD_PASS_CPW 2     // columns per consumer warp
+#endif
+#ifndef RBD_PASS_MT
+#define RBD_PASS_MT 256    // rows per tile (a multiple of 128)
+#endif
+#ifndef RBD_PASS_S2
+#define RBD_PASS_S2 5      // pipeline stages, FP64 input (two planes)
+#endif
+#ifndef RBD_PASS_S1
+#define RBD_PASS_S1 8      // pipeline stages, FP32 input (one plane)
+#endif
+#ifndef RBD_PASS_MINB
+#define RBD_PASS_MINB 1    // resident CTAs per SM the pass kernel is compiled for
+#endif
+
 namespace rbd {
 
 struct Ctl;
 
-// Fused-pass tile configuration, per number of FP32 planes (2 = FP64 input, 1 = FP32 input).
-// bf16 storage uses its own configuration (PassCfgBf16).
+// Fused-pass configuration per number of FP32 planes (2 = FP64 input, 1 = FP32 input).
 template <int P>
 struct PassCfg {
-    static constexpr int NW = 8;                 // consumer warps
-    static constexpr int CPW = 2;                // columns per consumer warp
+    static constexpr int NW = RBD_PASS_NW;
+    static constexpr int CPW = RBD_PASS_CPW;
     static constexpr int C = NW * CPW;           // columns per group
-    static constexpr int MT = 256;               // rows per tile (two 128-row slabs)
-    static constexpr int S = (P == 2) ? 5 : 8;   // pipeline stages
+    static constexpr int MT = RBD_PASS_MT;
+    static constexpr int NSLAB = MT / 128;
+    static constexpr int S = (P == 2) ? RBD_PASS_S2 : RBD_PASS_S1;
     static constexpr int XI_FLOATS = 2 * MT;     // split pivot-vector tile (hi, lo)
     static constexpr int STAGE_FLOATS = XI_FLOATS + C * P * MT;
     static constexpr int THREADS = (NW + 1) * 32;
     static constexpr size_t SCRATCH = 1024;
     static constexpr size_t SMEM = (size_t)S * STAGE_FLOATS * 4 + 2 * S * 8 + SCRATCH;
+    static_assert(MT % 128 == 0, "tile rows must be a multiple of 128");
 };
 
+// bf16 storage: one plane of 2-byte elements, plain FP32 accumulation.
 struct PassCfgBf16 {
     static constexpr int NW = 8;
     static constexpr int CPW = 2;
     static constexpr int C = NW * CPW;
     static constexpr int MT = 512;               // rows per tile (two 256-row slabs)
     static constexpr int S = 8;
-    static constexpr int XI_FLOATS = MT;         // hi part of the pivot vector only
+    static constexpr int XI_FLOATS = 2 * MT;
     static constexpr int STAGE_BYTES = XI_FLOATS * 4 + C * MT * 2;
     static constexpr int THREADS = (NW + 1) * 32;
     static constexpr size_t SCRATCH = 1024;
@@ -63,11 +91,13 @@ struct Work {
     // sizes
     int64_t m, n, ldx, ldp, d_max;
     int xt;                 // rbd_dtype
-    int planes_n;           // number of planes
+    int planes_n;           // number of planes P
     int esize;              // bytes per plane element
     // pass geometry
     int C, MT;
     int64_t NT, ngroups, W;
+    int64_t group_stride;   // elements per column group (C * P * ldp)
+    int64_t tile_stride;    // elements per full row tile of a group (C * P * MT)
     int G;                  // pass CTAs
     int KMAX;
     int64_t RB;             // row blocks of the GEMVs (ldp / 128)
@@ -79,7 +109,7 @@ struct Work {
     void* planes;
     float *yh, *yl;
     double *v1, *v2;
-    float *v1h, *v1l, *v2h, *v2l;
+    float *v1h, *v1l, *v2s;
     double *e, *xn2;
     double* vpart;
     double *hpart, *h;
@@ -94,8 +124,9 @@ struct Work {
     unsigned char* base;
 };
 
-// Fill sizes/geometry of `w` (no pointers); returns false on unsupported sizes.
-bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms);
+// Fill sizes/geometry of `w` (region offsets in the pointer fields); false on unsupported sizes.
+bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms,
+               int pass_ctas_per_sm);
 // Carve the regions of `w` out of `base` (at least w.total_bytes, 256-byte aligned).
 void carve_work(Work& w, void* base);
 
@@ -111,7 +142,8 @@ cudaError_t launch_pass(const Work& w, double* Y, int64_t ldy, double* T, int64_
                         uint32_t* progress, cudaStream_t st);
 cudaError_t launch_project(const double* Y, int64_t m, int64_t d, int64_t ldy, const void* V, int vt,
                            int64_t k, int64_t ldv, double* C, int64_t ldc, cudaStream_t st);
-// Dynamic shared-memory opt-in for the pass kernels (once per device).
-cudaError_t pass_kernel_setup();
+// Dynamic shared-memory opt-in for the pass kernels and their resident CTAs per SM, indexed by
+// storage type (once per device).
+cudaError_t pass_kernel_setup(int ctas_per_sm[3]);
 
 }  // namespace rbd
