@@ -168,12 +168,16 @@ rbd_status rbd_project(const double* Y, int64_t m, int64_t d, int64_t ldy,
    CUDA events recorded on the call's stream around each launch when profiling is enabled
    (rbd_set_profiling(1)).  Times are in milliseconds. */
 typedef struct rbd_profile {
-    int64_t pass_launches;   /* fused pass kernels (one per basis) */
-    double pass_ms;          /* their summed durations */
-    int64_t orth_launches;   /* orthogonalisation kernels */
+    int64_t pass_launches;   /* fused passes over X (one per basis) */
+    double pass_ms;          /* stepwise path: summed durations of the pass kernels */
+    int64_t orth_launches;   /* stepwise path: orthogonalisation kernels */
     double orth_ms;
     double init_ms;          /* the initial norm / re-layout pass */
-    int64_t pass_bytes;      /* algorithmic bytes of X streamed by the pass kernels */
+    int64_t pass_bytes;      /* algorithmic bytes of X streamed by the passes */
+    int64_t loop_launches;   /* persistent path: 1 (the whole greedy loop in one kernel) */
+    double loop_ms;          /* persistent path: duration of that kernel */
+    int32_t loop_kernel;     /* 1 if the persistent loop kernel ran, 0 for the stepwise path */
+    int32_t reserved;
 } rbd_profile;
 
 void rbd_set_profiling(int enabled);

@@ -28,7 +28,7 @@ static const int kLookahead = 4;
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms,
-               int pass_ctas_per_sm) {
+               int pass_ctas_per_sm, int loop_max_smem) {
     w = Work{};
     w.m = m;
     w.n = n;
@@ -55,9 +55,26 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     w.group_stride = (int64_t)w.C * w.planes_n * w.ldp;
     w.tile_stride = (int64_t)w.C * w.planes_n * w.MT;
     w.G = (int)std::min<int64_t>((int64_t)num_sms * std::max(1, pass_ctas_per_sm), w.W);
+    // The persistent loop kernel: one CTA per SM at most, each owning a block of R rows of Y.
+    w.use_loop = 0;
+    if (loop_max_smem > 0 && xt != RBD_BF16) {
+        const int64_t gl = std::min<int64_t>(num_sms, std::max<int64_t>(w.W, ceil_div(w.ldp, kLoopMaxRows)));
+        const int64_t R = round_up(ceil_div(w.ldp, gl), 4);
+        if (R <= kLoopMaxRows) {
+            const int LC = loop_chunk_cols_for(xt, (int)R);
+            const size_t smem = loop_smem_bytes(xt, (int)R, LC);
+            if (LC >= 4 && smem > 0 && smem <= (size_t)loop_max_smem) {
+                w.use_loop = 1;
+                w.G_loop = (int)gl;
+                w.R = (int)R;
+                w.LC = LC;
+                w.loop_smem = smem;
+            }
+        }
+    }
     // Largest number of CTAs sharing one column group.
     int64_t kmax = 1;
-    const int64_t G = w.G, W = w.W;
+    const int64_t G = w.use_loop ? w.G_loop : w.G, W = w.W;
     for (int64_t g = 0; g < w.ngroups; ++g) {
         const int64_t u0 = g * w.NT, u1 = g * w.NT + w.NT - 1;
         const int64_t b0 = ((u0 + 1) * G + W - 1) / W - 1;
@@ -84,20 +101,23 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     size_t o_lb = take((size_t)ceil_div(d_max, 8) * 4);
     size_t o_gc = take((size_t)w.ngroups * 4);
     w.zero_bytes = off;
+    const bool lp = w.use_loop != 0;
+    const size_t gp = (size_t)(lp ? w.G_loop : w.G);
     size_t o_planes = take((size_t)w.ngroups * (size_t)w.group_stride * w.esize);
-    size_t o_yh = take(ldp * (size_t)d_max * 4);
-    size_t o_yl = take(ldp * (size_t)d_max * 4);
-    size_t o_v1 = take(ldp * 8), o_v2 = take(ldp * 8);
-    size_t o_v1h = take(ldp * 4), o_v1l = take(ldp * 4);
+    size_t o_yh = take(lp ? 0 : ldp * (size_t)d_max * 4);
+    size_t o_yl = take(lp ? 0 : ldp * (size_t)d_max * 4);
+    size_t o_ysb = take(lp ? (size_t)w.G_loop * 2 * (size_t)d_max * (size_t)w.R * 4 : 0);
+    size_t o_v1 = take(lp ? 0 : ldp * 8), o_v2 = take(lp ? 0 : ldp * 8);
+    size_t o_v1h = take(lp ? 0 : ldp * 4), o_v1l = take(lp ? 0 : ldp * 4);
     size_t o_v2s = take((size_t)w.NT * 2 * w.MT * 4);
     size_t o_e = take((size_t)n * 8), o_xn2 = take((size_t)n * 8);
-    size_t o_vpart = take((size_t)w.LC_MAX * ldp * 8);
-    size_t o_hpart = take((size_t)w.RC_MAX * (size_t)d_max * 8);
+    size_t o_vpart = take(lp ? 0 : (size_t)w.LC_MAX * ldp * 8);
+    size_t o_hpart = take((size_t)(lp ? w.G_loop : w.RC_MAX) * (size_t)d_max * 8);
     size_t o_h = take((size_t)d_max * 8);
-    size_t o_nu2 = take((size_t)w.RB * 8);
+    size_t o_nu2 = take((size_t)std::max<int64_t>(w.RB, lp ? w.G_loop : 0) * 8);
     size_t o_gslot = take((size_t)w.ngroups * (size_t)w.KMAX * (size_t)w.C * 8);
     size_t o_gsum = take((size_t)w.ngroups * 8);
-    size_t o_pbe = take((size_t)w.G * 8), o_pbj = take((size_t)w.G * 8);
+    size_t o_pbe = take(gp * 8), o_pbj = take(gp * 8);
     w.total_bytes = off;
     // stash offsets in the pointer fields (carve_work rebases them)
     w.ctl = (Ctl*)o_ctl;
@@ -107,6 +127,7 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     w.planes = (void*)o_planes;
     w.yh = (float*)o_yh;
     w.yl = (float*)o_yl;
+    w.ysb = (float*)o_ysb;
     w.v1 = (double*)o_v1;
     w.v2 = (double*)o_v2;
     w.v1h = (float*)o_v1h;
@@ -136,6 +157,7 @@ void carve_work(Work& w, void* base) {
     RB_REBASE(planes);
     RB_REBASE(yh);
     RB_REBASE(yl);
+    RB_REBASE(ysb);
     RB_REBASE(v1);
     RB_REBASE(v2);
     RB_REBASE(v1h);
@@ -160,12 +182,20 @@ void carve_work(Work& w, void* base) {
 struct DeviceState {
     int num_sms = 0;
     int pass_ctas_per_sm[3] = {1, 1, 1};
+    int loop_max_smem = 0;  // 0: the persistent loop kernel is not used on this device
     bool ready = false;
 };
 static std::mutex g_dev_mu;
 static DeviceState g_dev[64];
 
-static cudaError_t device_state(int& num_sms, int* ctas_per_sm = nullptr) {
+// The stepwise path (one launch per kernel per basis) can be forced with RBD_STEPWISE=1; the
+// default is the persistent loop kernel whenever the device supports cooperative launches.
+static bool stepwise_forced() {
+    const char* v = getenv("RBD_STEPWISE");
+    return v && v[0] && v[0] != '0';
+}
+
+static cudaError_t device_state(DeviceState& out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -177,11 +207,19 @@ static cudaError_t device_state(int& num_sms, int* ctas_per_sm = nullptr) {
         if (e != cudaSuccess) return e;
         e = pass_kernel_setup(s.pass_ctas_per_sm);
         if (e != cudaSuccess) return e;
+        int coop = 0, optin = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (coop && optin > 0) {
+            if (loop_kernel_setup(optin) == cudaSuccess)
+                s.loop_max_smem = optin;
+            else
+                cudaGetLastError();
+        }
         s.ready = true;
     }
-    num_sms = s.num_sms;
-    if (ctas_per_sm)
-        for (int i = 0; i < 3; ++i) ctas_per_sm[i] = s.pass_ctas_per_sm[i];
+    out = s;
+    if (stepwise_forced()) out.loop_max_smem = 0;
     return cudaSuccess;
 }
 
@@ -255,11 +293,12 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
                                   double* T, int64_t ldt, int64_t* pivots, double* err, double* nu,
                                   void* workspace, size_t workspace_bytes, cudaStream_t st,
                                   rbd_result* result) {
-    int num_sms = 0, occ[3] = {1, 1, 1};
-    cudaError_t ce = device_state(num_sms, occ);
+    DeviceState ds;
+    cudaError_t ce = device_state(ds);
     if (ce != cudaSuccess) return map_cuda(ce);
     Work w;
-    if (!plan_work(w, m, n, ldx, d_max, (int)xt, num_sms, occ[(int)xt])) return RBD_EUNSUPPORTED;
+    if (!plan_work(w, m, n, ldx, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem))
+        return RBD_EUNSUPPORTED;
     if (xt == RBD_BF16) return RBD_EUNSUPPORTED;
 
     bool own = false;
@@ -308,9 +347,21 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
     }
     if (ce == cudaSuccess && prof) cudaEventRecord(ev_init1, st);
 
-    // orthogonalisation steps k = 0..d_max (the last one only certifies E_cur of basis
-    // d_max - 1 and takes the final stop decision); passes k = 0..d_max-1
-    for (int64_t k = 0; k <= d_max && ce == cudaSuccess; ++k) {
+    cudaEvent_t ev_loop0 = nullptr, ev_loop1 = nullptr;
+    if (w.use_loop && ce == cudaSuccess) {
+        // the whole greedy loop in one cooperative launch
+        if (prof) {
+            ev_loop0 = new_event();
+            ev_loop1 = new_event();
+            cudaEventRecord(ev_loop0, st);
+        }
+        ce = launch_loop(w, X, Y, ldy, T, ldt, pivots, err, nu, st);
+        ++launches;
+        if (prof) cudaEventRecord(ev_loop1, st);
+    }
+    // stepwise path: orthogonalisation steps k = 0..d_max (the last one only certifies E_cur of
+    // basis d_max - 1 and takes the final stop decision); passes k = 0..d_max-1
+    for (int64_t k = 0; !w.use_loop && k <= d_max && ce == cudaSuccess; ++k) {
         if (prog_h && k >= kLookahead) {
             // stay at most kLookahead steps ahead of the device; stop launching once it stopped
             volatile uint32_t* pr = prog_h;
@@ -407,7 +458,13 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
                 pf.pass_launches += 1;
             }
         }
+        if (ev_loop0 && cudaEventElapsedTime(&ms, ev_loop0, ev_loop1) == cudaSuccess) {
+            pf.loop_ms = ms;
+            pf.loop_launches = 1;
+            pf.pass_launches = dd;  // fused passes executed inside the loop kernel
+        }
         pf.pass_bytes = pf.pass_launches * m * n * (xt == RBD_F64 ? 8 : (xt == RBD_F32 ? 4 : 2));
+        pf.loop_kernel = w.use_loop;
         cudaGetLastError();
         t_profile = pf;
     }
@@ -448,13 +505,17 @@ extern "C" {
 
 size_t rbd_compress_workspace_bytes(int64_t m, int64_t n, int64_t d_max, rbd_dtype xt) {
     if (m < 1 || n < 1 || d_max < 1 || d_max > m || d_max > n || !valid_dtype((int)xt)) return 0;
-    int num_sms = 0, occ[3] = {RBD_PASS_MINB, RBD_PASS_MINB, 1};
-    if (device_state(num_sms, occ) != cudaSuccess) {
+    DeviceState ds;
+    if (device_state(ds) != cudaSuccess) {
+        // no device: the larger of the two paths' needs, planned for a 160-SM part
         cudaGetLastError();
-        num_sms = 160;  // upper bound for planning without a device
+        Work a, b;
+        if (!plan_work(a, m, n, m, d_max, (int)xt, 160, RBD_PASS_MINB, 232448)) return 0;
+        if (!plan_work(b, m, n, m, d_max, (int)xt, 160, RBD_PASS_MINB, 0)) return 0;
+        return std::max(a.total_bytes, b.total_bytes);
     }
     Work w;
-    if (!plan_work(w, m, n, m, d_max, (int)xt, num_sms, occ[(int)xt])) return 0;
+    if (!plan_work(w, m, n, m, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem)) return 0;
     return w.total_bytes;
 }
 

@@ -60,7 +60,15 @@ struct Ctl {
     int32_t mode;         // MODE_*
     int32_t pad1;
     int64_t d_max;
+    uint32_t bar[2];      // grid barrier of the persistent loop kernel {arrivals, generation}
 };
+
+// Element idx of X stored as FP64 (xt 0), FP32 (1) or BF16 (2), widened exactly to FP64.
+__device__ __forceinline__ double load_x_elem(const void* X, int xt, int64_t idx) {
+    if (xt == 0) return ((const double*)X)[idx];
+    if (xt == 1) return (double)((const float*)X)[idx];
+    return (double)__bfloat162float(((const __nv_bfloat16*)X)[idx]);
+}
 
 // --------------------------------------------------------------------------------------
 // float-float helpers
@@ -213,6 +221,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
+}
+
+// Orders this thread's generic-proxy global writes before later async-proxy (bulk copy) reads
+// of the same data.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // Named barrier over `nthreads` threads (a multiple of 32) with id `id` (1..15).

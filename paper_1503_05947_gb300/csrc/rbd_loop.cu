@@ -1,0 +1,849 @@
+// rbd_loop.cu -- the whole greedy loop of Algorithm 1 in ONE persistent cooperative kernel.
+//
+// One CTA per SM (8 consumer warps + 1 producer warp), all co-resident (cooperative launch), so
+// the steps of the loop are separated by grid-wide barriers instead of kernel launches.  Every
+// barrier and every mbarrier wait is bounded in time (kWaitLimitNs); a wait that runs out raises
+// RBD_ETIMEOUT in the control block and all CTAs leave the loop at the next barrier.
+//
+// Per basis k (k = 0 .. d_max; the last iteration only certifies E_cur and stops):
+//   O1   v1 = x_i - Y t, t = T(0:k, i)            rows of this CTA's block, float-float
+//   O1'  hpart[b] = Y_b' v1_b                      this CTA's partial re-orthogonalisation sums
+//   ---- grid barrier 1
+//   O2   h = sum_b hpart[b] (fixed order)          each CTA reduces k / G coefficients
+//   ---- grid barrier 2
+//   O3   v2 = v1 - Y h,  ||v2||^2 partial          float-float, as O1
+//   ---- grid barrier 3
+//   D    nu = ||v2|| (every CTA, fixed order); E_cur of basis k-1 = nu (the FP64 residual of the
+//        column that maximised the indicator); stop tests of steps 2.4 and 2.2, identical in
+//        every CTA
+//   P    the fused pass (rbd_tile.cuh): T(k, :), e_j, per-CTA argmax; Y(:, k) = v2 / nu for
+//        this CTA's rows
+//   ---- grid barrier 4
+//   A    argmax over the CTAs (every CTA), Frobenius residual (fixed order)
+//
+// This is classical Gram-Schmidt applied twice (see rbd_orth.cu for why, and for its accuracy);
+// Y is kept as a split FP32 copy stored ROW-BLOCK-MAJOR (block b = this CTA's R rows, all
+// columns contiguous), so each CTA streams only its own slice of Y, with bulk copies, and no
+// other CTA ever reads it.  X never changes, so the producer prefetches the first tiles of the
+// next pass while the orthogonalisation runs; only the pivot-vector tiles wait for O3.
+#include <algorithm>
+
+#include "rbd_device.cuh"
+#include "rbd_tile.cuh"
+#include "rbd_work.h"
+
+namespace rbd {
+
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;
+
+struct LoopParams {
+    int64_t m, n, ldp, ldx, ldt, ldy, d_max;
+    int xt;
+    // X planes (tile-major) and pass geometry
+    const float* planes;
+    int64_t group_stride, tile_stride, NT, ngroups, W;
+    int KMAX;
+    int evict_first;
+    // caller buffers
+    const void* X;
+    double* Y;
+    double* T;
+    int64_t* pivots;
+    double* err;
+    double* nu_out;
+    // workspace
+    Ctl* ctl;
+    uint32_t* bar;        // grid barrier {count, generation}
+    double* e;
+    const double* xn2;
+    float* ysb;           // [G][2][d_max][R] split Y, row-block-major
+    float* v2s;           // tile-interleaved split v2 (pivot-vector tiles of the pass)
+    double* hpart;        // [G][d_max]
+    double* h;            // [d_max]
+    double* nu2part;      // [G]
+    double* pbest_e;      // [G]
+    int64_t* pbest_j;     // [G]
+    uint32_t* gcnt;
+    double* gslot;
+    double* gsum;
+    int R;                // rows per CTA block (multiple of 4, <= kLoopMaxRows)
+    int LC;               // Y columns per streamed chunk (multiple of 4)
+};
+
+// ------------------------------------------------------------------------------------------
+// shared-memory layout (host and device agree through this function)
+// ------------------------------------------------------------------------------------------
+struct LoopSmem {
+    size_t bars, v1s, v2own, part, coef, v1split, scratch, total;
+};
+
+// Y columns per streamed chunk: both planes of LC x R floats fill at most one ring stage.
+template <int P>
+__host__ __device__ inline int loop_chunk_cols(int R) {
+    int lc = (PassCfg<P>::STAGE_FLOATS / 2) / R;
+    lc &= ~3;
+    if (lc > 256) lc = 256;
+    return lc;
+}
+
+template <int P>
+__host__ __device__ inline LoopSmem loop_smem_layout(int R, int LC) {
+    using Cfg = PassCfg<P>;
+    LoopSmem s;
+    size_t o = (size_t)Cfg::S * Cfg::STAGE_FLOATS * 4;  // the ring: pass stages / Y chunks
+    s.bars = o;
+    o += (size_t)(3 * Cfg::S) * 8;                // full, empty, ybar
+    s.v1s = o;
+    o += (size_t)R * 8;
+    s.v2own = o;
+    o += (size_t)R * 8;
+    s.part = o;
+    o += (size_t)(R > 256 ? R : 256) * 8;
+    s.coef = o;
+    o += (size_t)Cfg::S * 2 * LC * 4;             // per ring buffer: (hi, lo) x LC
+    s.v1split = o;
+    o += (size_t)2 * R * 4;
+    s.scratch = o;
+    o += (size_t)(2 * Cfg::NW + 2 * Cfg::C + 8) * 8;
+    s.total = (o + 127) & ~size_t(127);
+    return s;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch; called by every thread of every CTA.  Returns
+// false in all threads of a CTA whose wait ran out (the caller then leaves the loop).
+__device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint32_t& gen, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint32_t my = gen;
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            st_release_u32(&bar[1], my + 1);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_acquire_u32(&bar[1]) == my) {
+                if (globaltimer_ns() - t0 > kBarrierLimitNs) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        gen = my + 1;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Streams columns [0, k) of this CTA's Y slice, LC columns at a time, through the NB stage
+// buffers of the pass ring (idle during the orthogonalisation), up to NB chunks in flight.
+// Bulk copies are issued by consumer thread 0 and complete on ybar[buffer]; body(yh, yl, ch,
+// cl, l0, lc) runs for each chunk with all consumers; load_coef(l, hi, lo) gives the
+// coefficient of column l (staged in shared memory next to the chunk).  np = planes streamed.
+struct YStream {
+    float* ring;        // NB buffers of buf_floats floats
+    int buf_floats;
+    int NB;
+    uint64_t* ybar;     // NB barriers
+    float* coef;        // NB x 2 x LC
+    const float* ysb_b; // this CTA's block of the split Y
+    int64_t d_max;
+    int R, LC;
+    uint64_t pol;
+    uint32_t count;     // chunks streamed so far (all calls): fixes each chunk's buffer and parity
+    bool loaded;        // the slice of this step is resident in the ring
+    int64_t nloaded;
+    bool* ok;
+};
+
+template <int NCONS, class Coef, class Body>
+__device__ __forceinline__ void ystream(YStream& ys, int64_t k, int np, int tid, Ctl* ctl, Coef&& load_coef,
+                                        Body&& body) {
+    const int64_t nch = ceil_div(k, ys.LC);
+    if (nch == 0) return;
+    const int plane = ys.LC * ys.R;  // floats: offset of plane 1 inside a buffer
+    auto bufof = [&](int64_t c) { return (int)((ys.count + (uint32_t)c) % (uint32_t)ys.NB); };
+    auto issue = [&](int64_t c) {
+        const int bf = bufof(c);
+        const int64_t l0 = c * ys.LC;
+        const int lc = (int)min((int64_t)ys.LC, k - l0);
+        const uint32_t bytes = (uint32_t)lc * (uint32_t)ys.R * 4u;
+        mbar_arrive_expect_tx(&ys.ybar[bf], (uint32_t)np * bytes);
+        for (int pl = 0; pl < np; ++pl)
+            bulk_g2s(ys.ring + (size_t)bf * ys.buf_floats + (size_t)pl * plane,
+                     ys.ysb_b + ((int64_t)pl * ys.d_max + l0) * ys.R, bytes, &ys.ybar[bf], ys.pol);
+    };
+    auto stage_coef = [&](int64_t c) {
+        const int bf = bufof(c);
+        const int64_t l0 = c * ys.LC;
+        const int lc = (int)min((int64_t)ys.LC, k - l0);
+        for (int l = tid; l < lc; l += NCONS) {
+            float hi, lo;
+            load_coef(l0 + l, hi, lo);
+            ys.coef[(bf * 2 + 0) * ys.LC + l] = hi;
+            ys.coef[(bf * 2 + 1) * ys.LC + l] = lo;
+        }
+    };
+    // Resident mode: when the whole slice fits in the ring (nch <= NB) it is loaded by the first
+    // call of a step and reused by the later calls of the same step (ystream_end_step releases it).
+    const bool resident = nch <= ys.NB;
+    const bool reuse = resident && ys.loaded;
+    const int64_t npre = min(nch, (int64_t)ys.NB);
+    if (tid == 0 && !reuse)
+        for (int64_t c = 0; c < npre; ++c) issue(c);
+    for (int64_t c = 0; c < npre; ++c) stage_coef(c);
+    for (int64_t c = 0; c < nch; ++c) {
+        named_bar(1, NCONS);  // coefficients visible; chunk c-1 consumed, so its buffer is free
+        if (!resident && c >= 1 && c - 1 + ys.NB < nch) {
+            if (tid == 0) issue(c - 1 + ys.NB);
+            stage_coef(c - 1 + ys.NB);
+        }
+        const int bf = bufof(c);
+        const uint32_t par = ((ys.count + (uint32_t)c) / (uint32_t)ys.NB) & 1u;
+        if (!reuse && *ys.ok && !mbar_wait(&ys.ybar[bf], par)) {
+            raise_status(ctl, ST_ETIMEOUT);
+            *ys.ok = false;
+        }
+        const int64_t l0 = c * ys.LC;
+        const int lc = (int)min((int64_t)ys.LC, k - l0);
+        if (*ys.ok)
+            body(ys.ring + (size_t)bf * ys.buf_floats, ys.ring + (size_t)bf * ys.buf_floats + plane,
+                 ys.coef + (bf * 2) * ys.LC, ys.coef + (bf * 2 + 1) * ys.LC, l0, lc);
+    }
+    named_bar(1, NCONS);  // the last chunk is consumed before the ring is reused
+    if (resident) {
+        ys.loaded = true;
+        ys.nloaded = nch;
+    } else {
+        ys.count += (uint32_t)nch;
+    }
+}
+
+// End of the orthogonalisation of a step: a resident slice gives its buffers back to the ring.
+__device__ __forceinline__ void ystream_end_step(YStream& ys) {
+    if (ys.loaded) {
+        ys.count += (uint32_t)ys.nloaded;
+        ys.loaded = false;
+        ys.nloaded = 0;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) loop_kernel(LoopParams p) {
+    using Cfg = PassCfg<P>;
+    constexpr int NW = Cfg::NW, CPW = Cfg::CPW, C = Cfg::C, MT = Cfg::MT, S = Cfg::S;
+    constexpr int XI = Cfg::XI_FLOATS, STAGE = Cfg::STAGE_FLOATS;
+    constexpr int NCONS = NW * 32;
+    constexpr int MAXRPT = kLoopMaxRows / NCONS;  // rows per consumer thread when R > NCONS
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const LoopSmem L = loop_smem_layout<P>(p.R, p.LC);
+    float* stages = reinterpret_cast<float*>(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bars);
+    uint64_t* empty = full + S;
+    uint64_t* ybar = empty + S;
+    double* v1s = reinterpret_cast<double*>(smem_raw + L.v1s);
+    double* v2own = reinterpret_cast<double*>(smem_raw + L.v2own);
+    double* part = reinterpret_cast<double*>(smem_raw + L.part);
+    float* coef = reinterpret_cast<float*>(smem_raw + L.coef);
+    float* v1h = reinterpret_cast<float*>(smem_raw + L.v1split);
+    float* v1l = v1h + p.R;
+    double* red_e = reinterpret_cast<double*>(smem_raw + L.scratch);  // NW
+    int64_t* red_j = reinterpret_cast<int64_t*>(red_e + NW);          // NW
+    double* grp_e = reinterpret_cast<double*>(red_j + NW);           // 2 C
+    double* bcast = grp_e + 2 * C;                                   // 4 doubles
+    int* sflags = reinterpret_cast<int*>(bcast + 4);                 // 8 ints
+
+    Ctl* ctl = p.ctl;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t G = gridDim.x, b = blockIdx.x;
+    const int R = p.R;
+    const int64_t r0 = b * (int64_t)R;
+    const int Rb = (int)max((int64_t)0, min((int64_t)R, p.ldp - r0));  // rows of this block within ldp
+    const int64_t W = p.W, NT = p.NT;
+    const int64_t L0 = (W * b) / G, L1 = (W * (b + 1)) / G;
+    const int64_t nunits = L1 - L0;
+
+    if (ctl->status != 0 || ctl->stop != 0) return;  // set by the initial pass, uniform
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 2);    // X part and pivot-vector part arrive separately
+            mbar_init(&empty[s], NW);
+            mbar_init(&ybar[s], 1);    // Y chunks streamed through the same buffers
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    bool ok = true;
+    uint32_t gen = 0;
+    YStream ys;
+    ys.ring = stages;
+    ys.buf_floats = STAGE;
+    ys.NB = S;
+    ys.ybar = ybar;
+    ys.coef = coef;
+    ys.ysb_b = p.ysb + b * 2 * p.d_max * (int64_t)R;
+    ys.d_max = p.d_max;
+    ys.R = R;
+    ys.LC = p.LC;
+    ys.pol = l2_policy_evict_normal();
+    ys.count = 0;
+    ys.loaded = false;
+    ys.nloaded = 0;
+    ys.ok = &ok;
+
+    // pass pipeline state (producer and consumers advance identical copies)
+    int ps = 0;
+    uint32_t pph = 0;
+    bool preuse = false;  // producer
+    int cs = 0;
+    uint32_t cph = 0;     // consumers
+    int64_t npref = 0;    // producer: units of the next pass whose X tiles are in flight
+    int pf_s0 = 0;        // stage and phase parity of the first prefetched unit
+    uint32_t pf_ph0 = 0;
+
+    int64_t piv = ctl->pivot;
+    double fro_prev = ctl->fro_last;
+    const int mode = ctl->mode;
+    const double eps_r = ctl->eps_r, eps_r22 = ctl->eps_r22, fro_tol = ctl->fro_tol;
+    const float* planes = p.planes;
+    const uint64_t pol_x = p.evict_first ? l2_policy_evict_first() : l2_policy_evict_normal();
+    const uint64_t pol_xi = l2_policy_evict_normal();
+
+    int64_t k = 0;
+    int32_t stop = STOP_NONE;
+    double nu = 0.0;
+    for (;; ++k) {
+        // ---------------- O1 / O1': v1 = x_i - Y t, partial h = Y_b' v1_b ----------------
+        const int NSUB = (R <= NCONS) ? (NCONS / R) : 1;
+        const int q = (R <= NCONS) ? (tid / R) : 0;
+        const int rfirst = (R <= NCONS) ? (tid % R) : tid;
+        const bool active = (warp < NW) && ((R <= NCONS) ? (tid < NSUB * R) : true);
+        if (warp < NW) {
+            // the pivot column's rows of this block, loaded now so the loads overlap the stream
+            // (v2own is free until O3; each thread later reads back only the rows it loaded)
+            for (int r = tid; r < R; r += NCONS)
+                v2own[r] = (r < Rb && r0 + r < p.m) ? load_x_elem(p.X, p.xt, piv * p.ldx + r0 + r) : 0.0;
+            float as[MAXRPT], ac[MAXRPT];
+#pragma unroll
+            for (int i = 0; i < MAXRPT; ++i) as[i] = ac[i] = 0.f;
+            if (k > 0) {
+                const double* tcol = p.T + piv * p.ldt;
+                ystream<NCONS>(
+                    ys, k, 2, tid, ctl,
+                    [&](int64_t l, float& hi, float& lo) { split_double(__ldcg(&tcol[l]), hi, lo); },
+                    [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
+                        if (!active) return;
+#pragma unroll
+                        for (int i = 0; i < MAXRPT; ++i) {
+                            const int r = rfirst + i * NCONS;
+                            if (r >= Rb || (R <= NCONS && i > 0)) break;
+                            for (int l = q; l < lc; l += NSUB)
+                                ff_mac2(as[i], ac[i], yh[l * R + r], yl[l * R + r], ch[l], cl[l]);
+                        }
+                    });
+            }
+            // combine the column subsets and finish v1 for this block's rows
+            if (R <= NCONS) {
+                if (active) part[q * R + rfirst] = ff_to_double(as[0], ac[0]);
+                named_bar(1, NCONS);
+                for (int r = tid; r < R; r += NCONS) {
+                    double v = 0.0;
+                    if (r < Rb && r0 + r < p.m) {
+                        double acc = 0.0;
+                        for (int qq = 0; qq < NSUB; ++qq) acc += part[qq * R + r];
+                        v = v2own[r] - acc;
+                    }
+                    v1s[r] = v;
+                    split_double(v, v1h[r], v1l[r]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < MAXRPT; ++i) {
+                    const int r = rfirst + i * NCONS;
+                    if (r >= R) break;
+                    double v = 0.0;
+                    if (r < Rb && r0 + r < p.m) v = v2own[r] - ff_to_double(as[i], ac[i]);
+                    v1s[r] = v;
+                    split_double(v, v1h[r], v1l[r]);
+                }
+            }
+            named_bar(1, NCONS);
+            if (k > 0) {
+                ystream<NCONS>(
+                    ys, k, 2, tid, ctl, [&](int64_t, float& hi, float& lo) { hi = lo = 0.f; },
+                    [&](const float* yh, const float* yl, const float*, const float*, int64_t l0, int lc) {
+                        // four consecutive threads share a column, each summing a quarter of the
+                        // rows; the quarters are combined in float-float inside the quad
+                        const int quad = tid & 3, lq = tid >> 2;
+                        const int rq = (Rb + 3) >> 2;
+                        const int ra = quad * rq, rz = min(Rb, ra + rq);
+                        for (int lb = 0; lb < lc; lb += NCONS / 4) {
+                            const int l = lb + lq;
+                            float s = 0.f, c = 0.f;
+                            if (l < lc)
+                                for (int r = ra; r < rz; ++r) ff_mac2(s, c, yh[l * R + r], yl[l * R + r], v1h[r], v1l[r]);
+#pragma unroll
+                            for (int o = 1; o < 4; o <<= 1) {
+                                const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+                                const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+                                ff_add(s, c, s2, c2);
+                            }
+                            if (l < lc && quad == 0) p.hpart[b * p.d_max + l0 + l] = ff_to_double(s, c);
+                        }
+                    });
+            }
+        }
+        if (k > 0) {
+            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;   // barrier 1
+            if (!ok || __ldcg(&ctl->status) != 0) break;
+            // ---------------- O2: h(l) = sum_b hpart[b](l), k / G coefficients per CTA ----------------
+            if (warp < NW) {
+                const int64_t lb0 = (k * b) / G, lb1 = (k * (b + 1)) / G;
+                for (int64_t l = lb0 + warp; l < lb1; l += NW) {
+                    double acc = 0.0;
+                    #pragma unroll 8
+                    for (int64_t bb = lane; bb < G; bb += 32) acc += __ldcg(&p.hpart[bb * p.d_max + l]);
+                    acc = warp_sum_double(acc);
+                    if (lane == 0) p.h[l] = acc;
+                }
+            }
+            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;   // barrier 2
+            if (!ok || __ldcg(&ctl->status) != 0) break;
+        }
+
+        // ---------------- O3: v2 = v1 - Y h, ||v2||^2 partial ----------------
+        // float-float as in O1: when the pivot nearly lies in span(Y), ||v1|| is tiny and h is
+        // not small relative to it, so Y h needs the full precision for Y'Y = I to hold.
+        if (warp < NW) {
+            float as[MAXRPT], ac[MAXRPT];
+#pragma unroll
+            for (int i = 0; i < MAXRPT; ++i) as[i] = ac[i] = 0.f;
+            if (k > 0) {
+                ystream<NCONS>(
+                    ys, k, 2, tid, ctl,
+                    [&](int64_t l, float& hi, float& lo) { split_double(__ldcg(&p.h[l]), hi, lo); },
+                    [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
+                        if (!active) return;
+#pragma unroll
+                        for (int i = 0; i < MAXRPT; ++i) {
+                            const int r = rfirst + i * NCONS;
+                            if (r >= Rb || (R <= NCONS && i > 0)) break;
+                            for (int l = q; l < lc; l += NSUB)
+                                ff_mac2(as[i], ac[i], yh[l * R + r], yl[l * R + r], ch[l], cl[l]);
+                        }
+                    });
+            }
+            if (R <= NCONS) {
+                if (active) part[q * R + rfirst] = ff_to_double(as[0], ac[0]);
+                named_bar(1, NCONS);
+                for (int r = tid; r < R; r += NCONS) {
+                    double corr = 0.0;
+                    for (int qq = 0; qq < NSUB; ++qq) corr += part[qq * R + r];
+                    v2own[r] = (r < Rb) ? v1s[r] - corr : 0.0;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < MAXRPT; ++i) {
+                    const int r = rfirst + i * NCONS;
+                    if (r >= R) break;
+                    v2own[r] = (r < Rb) ? v1s[r] - ff_to_double(as[i], ac[i]) : 0.0;
+                }
+            }
+            named_bar(1, NCONS);
+            // split copy for the pass (tile-interleaved), and ||v2||^2 of this block (fixed order)
+            for (int r = tid; r < Rb; r += NCONS) {
+                const int64_t row = r0 + r;
+                const int64_t t = row / MT;
+                const int64_t rt = min((int64_t)MT, p.ldp - t * MT);
+                const int64_t off = t * 2 * MT + (row - t * MT);
+                float hi, lo;
+                split_double(v2own[r], hi, lo);
+                p.v2s[off] = hi;
+                p.v2s[off + rt] = lo;
+            }
+            fence_proxy_async_global();  // v2s is read by bulk copies in the pass
+            if (warp == 0) {
+                double acc = 0.0;
+                for (int r = lane; r < Rb; r += 32) acc += v2own[r] * v2own[r];
+                acc = warp_sum_double(acc);
+                if (lane == 0) p.nu2part[b] = acc;
+            }
+        }
+        // ---------------- producer: prefetch the X tiles of pass k ----------------
+        // The ring is free once every consumer is past O3; X never changes, so its first tiles
+        // load while the CTAs synchronise and take the stop decision.
+        ystream_end_step(ys);
+        __syncthreads();
+        if (warp == NW) {
+            if (lane == 0 && k < p.d_max && ok) {
+                npref = min(nunits, (int64_t)S);
+                pf_s0 = ps;
+                pf_ph0 = pph;
+                int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
+                for (int64_t i = 0; i < npref; ++i) {
+                    if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                        raise_status(ctl, ST_ETIMEOUT);
+                        ok = false;
+                        npref = i;
+                        break;
+                    }
+                    const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                    const uint32_t x_bytes = (uint32_t)(C * P) * rows * 4u;
+                    float* st = stages + (size_t)ps * STAGE;
+                    mbar_arrive_expect_tx(&full[ps], x_bytes);
+                    bulk_g2s(st + XI, planes + g * p.group_stride + t * p.tile_stride, x_bytes, &full[ps], pol_x);
+                    if (++ps == S) {
+                        ps = 0;
+                        pph ^= 1u;
+                        preuse = true;
+                    }
+                    if (++t == NT) {
+                        t = 0;
+                        ++g;
+                    }
+                }
+            }
+        }
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 3
+        if (!ok || __ldcg(&ctl->status) != 0) break;
+
+        // ---------------- D: nu, certified E_cur of basis k-1, stop tests ----------------
+        if (warp == 0) {
+            double acc = 0.0;
+            #pragma unroll 8
+            for (int64_t bb = lane; bb < G; bb += 32) acc += __ldcg(&p.nu2part[bb]);
+            acc = warp_sum_double(acc);
+            if (lane == 0) {
+                const double nuv = sqrt(acc);
+                const double xin = sqrt(p.xn2[piv]);
+                int32_t st = STOP_NONE;
+                if (k > 0) {
+                    if (mode == MODE_FRO_REL) {
+                        if (__ldcg(&ctl->fro_last) <= fro_tol) st = STOP_TOL;
+                    } else if (nuv <= eps_r) {
+                        st = STOP_TOL;
+                    }
+                }
+                if (st == STOP_NONE && k >= p.d_max) st = STOP_DMAX;
+                if (st == STOP_NONE && (nuv < eps_r22 || nuv <= kRankFloor * xin)) st = STOP_BREAK;
+                bcast[0] = nuv;
+                sflags[1] = st;
+                if (b == 0) {
+                    if (k > 0) {
+                        p.err[k - 1] = nuv;
+                        ctl->err_last = nuv;
+                    }
+                    if (st == STOP_NONE) {
+                        p.pivots[k] = piv;
+                        if (p.nu_out) p.nu_out[k] = nuv;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        nu = bcast[0];
+        stop = sflags[1];
+        if (stop != STOP_NONE) break;
+
+        // ---------------- P: the fused pass of basis k ----------------
+        const double inv_nu = 1.0 / nu;
+        // Y(:, k) = v2 / nu for this block's rows (user Y and the split row-block copy)
+        for (int r = tid; r < Rb; r += Cfg::THREADS) {
+            const double y = v2own[r] * inv_nu;
+            if (r0 + r < p.m) p.Y[(r0 + r) + k * p.ldy] = y;
+            float hi, lo;
+            split_double(y, hi, lo);
+            p.ysb[(b * 2 + 0) * p.d_max * R + k * R + r] = hi;
+            p.ysb[(b * 2 + 1) * p.d_max * R + k * R + r] = lo;
+        }
+        fence_proxy_async_global();  // this block of Y is streamed by bulk copies in later steps
+        if (warp == NW) {
+            // producer: pivot-vector tiles of the prefetched units, then the remaining units
+            if (lane == 0 && ok) {
+                int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
+                int sp = pf_s0;  // stage of the first prefetched unit
+                for (int64_t i = 0; i < npref; ++i) {
+                    const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                    const uint32_t xi_bytes = 2u * rows * 4u;
+                    mbar_arrive_expect_tx(&full[sp], xi_bytes);
+                    bulk_g2s(stages + (size_t)sp * STAGE, p.v2s + t * 2 * MT, xi_bytes, &full[sp], pol_xi);
+                    if (++sp == S) sp = 0;
+                    if (++t == NT) {
+                        t = 0;
+                        ++g;
+                    }
+                }
+                for (int64_t i = npref; i < nunits; ++i) {
+                    if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                        raise_status(ctl, ST_ETIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                    const uint32_t xi_bytes = 2u * rows * 4u;
+                    const uint32_t x_bytes = (uint32_t)(C * P) * rows * 4u;
+                    float* st = stages + (size_t)ps * STAGE;
+                    mbar_arrive_expect_tx(&full[ps], x_bytes);
+                    bulk_g2s(st + XI, planes + g * p.group_stride + t * p.tile_stride, x_bytes, &full[ps], pol_x);
+                    mbar_arrive_expect_tx(&full[ps], xi_bytes);
+                    bulk_g2s(st, p.v2s + t * 2 * MT, xi_bytes, &full[ps], pol_xi);
+                    if (++ps == S) {
+                        ps = 0;
+                        pph ^= 1u;
+                        preuse = true;
+                    }
+                    if (++t == NT) {
+                        t = 0;
+                        ++g;
+                    }
+                }
+                npref = 0;
+            }
+        } else {
+            // consumers
+            float acc_s[CPW][4], acc_c[CPW][4];
+#pragma unroll
+            for (int qq = 0; qq < CPW; ++qq)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
+            double best_e = -1.0;
+            int64_t best_j = INT64_MAX;
+            double e_old[CPW];
+#pragma unroll
+            for (int qq = 0; qq < CPW; ++qq) e_old[qq] = 0.0;
+            int gbuf = 0;
+            FlushCtx fc;
+            fc.T = p.T;
+            fc.ldt = p.ldt;
+            fc.e = p.e;
+            fc.n = p.n;
+            fc.k = k;
+            fc.piv = piv;
+            fc.inv_nu = inv_nu;
+            fc.gcnt = p.gcnt;
+            fc.gslot = p.gslot;
+            fc.gsum = p.gsum;
+            fc.KMAX = p.KMAX;
+            fc.W = W;
+            fc.NT = NT;
+            fc.G = G;
+            fc.b = b;
+            fc.L0 = L0;
+            fc.L1 = L1;
+            fc.grp_e = grp_e;
+            fc.flag = &sflags[2];
+            int64_t g_next = L0 / NT, t_next = L0 - (L0 / NT) * NT;
+            for (int64_t u = L0; u < L1; ++u) {
+                const int64_t g = g_next, t = t_next;
+                const int s = cs;
+                const uint32_t ph = cph;
+                if (++cs == S) {
+                    cs = 0;
+                    cph ^= 1u;
+                }
+                if (++t_next == NT) {
+                    t_next = 0;
+                    ++g_next;
+                }
+                const int64_t c0 = g * C;
+                const int ncols = (int)min((int64_t)C, p.n - c0);
+                if (lane == 0 && (t == 0 || u == L0)) {
+#pragma unroll
+                    for (int qq = 0; qq < CPW; ++qq) {
+                        const int cw = warp * CPW + qq;
+                        if (cw < ncols) e_old[qq] = __ldcg(&p.e[c0 + cw]);
+                    }
+                }
+                if (ok && !mbar_wait(&full[s], ph)) {
+                    raise_status(ctl, ST_ETIMEOUT);
+                    ok = false;
+                }
+                const int rows = (int)min((int64_t)MT, p.ldp - t * MT);
+                if (ok) {
+                    const float* st = stages + (size_t)s * STAGE;
+                    if (rows == MT)
+                        consume_tile<P, CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
+                    else
+                        consume_tile<P, CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+                if (t != NT - 1 && u != L1 - 1) continue;
+                flush_group<CPW, C, NCONS>(fc, g, warp, lane, tid, acc_s, acc_c, e_old, best_e, best_j, gbuf);
+            }
+            if (lane == 0) {
+                red_e[warp] = best_e;
+                red_j[warp] = best_j;
+            }
+            named_bar(1, NCONS);
+            if (tid == 0) {
+                double be = -1.0;
+                int64_t bj = INT64_MAX;
+                for (int w = 0; w < NW; ++w)
+                    if (better(red_e[w], red_j[w], be, bj)) {
+                        be = red_e[w];
+                        bj = red_j[w];
+                    }
+                p.pbest_e[b] = be;
+                p.pbest_j[b] = bj;
+            }
+        }
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 4
+        if (!ok || __ldcg(&ctl->status) != 0) break;
+
+        // ---------------- A: argmax over CTAs, Frobenius residual ----------------
+        if (warp == 0) {
+            double be = -1.0;
+            int64_t bj = INT64_MAX;
+            #pragma unroll 8
+            for (int64_t cb = lane; cb < G; cb += 32) {
+                const double ce = __ldcg(&p.pbest_e[cb]);
+                const int64_t cj = __ldcg(reinterpret_cast<const long long*>(&p.pbest_j[cb]));
+                if (better(ce, cj, be, bj)) {
+                    be = ce;
+                    bj = cj;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double oe = __shfl_down_sync(0xffffffffu, be, o);
+                const int64_t oj = __shfl_down_sync(0xffffffffu, bj, o);
+                if (better(oe, oj, be, bj)) {
+                    be = oe;
+                    bj = oj;
+                }
+            }
+            // Frobenius residual (fixed order): CTA 0 only; it publishes it in the control block,
+            // where the other CTAs read it in the next step's phase D
+            double fs = 0.0;
+            if (b == 0) {
+#pragma unroll 8
+                for (int64_t gg = lane; gg < p.ngroups; gg += 32) fs += __ldcg(&p.gsum[gg]);
+                fs = warp_sum_double(fs);
+            }
+            if (lane == 0) {
+                bcast[1] = sqrt(fmax(fs, 0.0));
+                bcast[2] = sqrt(fmax(be, 0.0));
+                red_j[0] = (bj >= 0 && bj < p.n) ? bj : piv;
+            }
+        }
+        __syncthreads();
+        if (b == 0) fro_prev = bcast[1];
+        piv = red_j[0];
+        if (b == 0 && tid == 0) {
+            ctl->d = k + 1;
+            ctl->pivot = piv;
+            ctl->fro_last = fro_prev;
+            ctl->err_downdate = bcast[2];
+        }
+        __syncthreads();
+    }
+
+    // ---------------- leave: drain prefetched tiles, publish the final state ----------------
+    if (warp == NW && lane == 0 && npref > 0) {
+        // The loop stopped after the X tiles of the next pass were prefetched: complete those
+        // stages' phases (second arrival, no pivot-vector part) and wait for the X tiles to
+        // land, so that no bulk copy into this CTA's shared memory is in flight at exit.
+        for (int64_t i = 0; i < npref; ++i) {
+            const int64_t si = pf_s0 + i;
+            const int sp = (int)(si % S);
+            const uint32_t par = pf_ph0 ^ (uint32_t)((si / S) & 1);
+            mbar_arrive(&full[sp]);
+            if (!mbar_wait(&full[sp], par)) {
+                raise_status(ctl, ST_ETIMEOUT);
+                break;
+            }
+        }
+    }
+    if (b == 0 && tid == 0) {
+        if (stop != STOP_NONE) {
+            ctl->stop = stop;
+            ctl->d = k;
+            ctl->pivot = piv;
+            ctl->fro_last = fro_prev;
+        }
+    }
+}
+
+int loop_chunk_cols_for(int xt, int R) {
+    if (xt == 0) return loop_chunk_cols<2>(R);
+    if (xt == 1) return loop_chunk_cols<1>(R);
+    return 0;
+}
+
+size_t loop_smem_bytes(int xt, int R, int LC) {
+    if (xt == 0) return loop_smem_layout<2>(R, LC).total;
+    if (xt == 1) return loop_smem_layout<1>(R, LC).total;
+    return 0;
+}
+
+cudaError_t loop_kernel_setup(int max_smem) {
+    cudaError_t e = cudaFuncSetAttribute(loop_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(loop_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    return e;
+}
+
+cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, double* T, int64_t ldt,
+                        int64_t* pivots, double* err, double* nu_out, cudaStream_t st) {
+    LoopParams p;
+    p.m = w.m;
+    p.n = w.n;
+    p.ldp = w.ldp;
+    p.ldx = w.ldx;
+    p.ldt = ldt;
+    p.ldy = ldy;
+    p.d_max = w.d_max;
+    p.xt = w.xt;
+    p.planes = static_cast<const float*>(w.planes);
+    p.group_stride = w.group_stride;
+    p.tile_stride = w.tile_stride;
+    p.NT = w.NT;
+    p.ngroups = w.ngroups;
+    p.W = w.W;
+    p.KMAX = w.KMAX;
+    p.evict_first = w.evict_first;
+    p.X = X;
+    p.Y = Y;
+    p.T = T;
+    p.pivots = pivots;
+    p.err = err;
+    p.nu_out = nu_out;
+    p.ctl = w.ctl;
+    p.bar = w.ctl->bar;
+    p.e = w.e;
+    p.xn2 = w.xn2;
+    p.ysb = w.ysb;
+    p.v2s = w.v2s;
+    p.hpart = w.hpart;
+    p.h = w.h;
+    p.nu2part = w.nu2part;
+    p.pbest_e = w.pbest_e;
+    p.pbest_j = w.pbest_j;
+    p.gcnt = w.gcnt;
+    p.gslot = w.gslot;
+    p.gsum = w.gsum;
+    p.R = w.R;
+    p.LC = w.LC;
+    void* args[] = {&p};
+    const void* fn = (w.xt == 0) ? (const void*)loop_kernel<2> : (const void*)loop_kernel<1>;
+    const int threads = (w.xt == 0) ? PassCfg<2>::THREADS : PassCfg<1>::THREADS;
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)w.G_loop), dim3((unsigned)threads), args, w.loop_smem, st);
+}
+
+}  // namespace rbd

@@ -26,6 +26,7 @@
 //   * The per-CTA argmax candidates are combined by the last CTA to finish, which names the
 //     next pivot and publishes the step count to the host-mapped progress word.
 #include "rbd_device.cuh"
+#include "rbd_tile.cuh"
 #include "rbd_work.h"
 
 namespace rbd {
@@ -56,48 +57,6 @@ struct PassParams {
     int evict_first;
     uint32_t* progress;       // host-mapped {steps finished, stop} (may be null)
 };
-
-// CTA that processes unit u when W units are split into G contiguous ranges
-// [floor(b W / G), floor((b + 1) W / G)).
-__device__ __forceinline__ int64_t unit_owner(int64_t u, int64_t W, int64_t G) {
-    return ((u + 1) * G + W - 1) / W - 1;
-}
-
-// Float-float dot-product contributions of one staged tile for this warp's CPW columns.
-// Stage layout: [xi hi (rows) | xi lo (rows) | pad to 2*MT | column c plane p at (c*P + p)*rows].
-// FULL tiles (rows == MT) compile to straight-line code; the ragged last row tile of a column
-// group takes the generic path.
-template <int P, int CPW, int MT, bool FULL>
-__device__ __forceinline__ void consume_tile(const float* __restrict__ st, int rows, int warp, int lane,
-                                             float (&acc_s)[CPW][4], float (&acc_c)[CPW][4]) {
-    constexpr int XI = 2 * MT;
-    const int R = FULL ? MT : rows;
-    const int nsl = FULL ? MT / 128 : (rows >> 7);
-#pragma unroll
-    for (int sl = 0; sl < MT / 128; ++sl) {
-        if (!FULL && sl >= nsl) break;
-        const int off = sl * 128 + lane * 4;
-        const float4 zh = *reinterpret_cast<const float4*>(st + off);
-        const float4 zl = *reinterpret_cast<const float4*>(st + R + off);
-#pragma unroll
-        for (int q = 0; q < CPW; ++q) {
-            const float* col = st + XI + (warp * CPW + q) * P * R + off;
-            const float4 a = *reinterpret_cast<const float4*>(col);
-            if (P == 2) {
-                const float4 al = *reinterpret_cast<const float4*>(col + R);
-                ff_mac2(acc_s[q][0], acc_c[q][0], a.x, al.x, zh.x, zl.x);
-                ff_mac2(acc_s[q][1], acc_c[q][1], a.y, al.y, zh.y, zl.y);
-                ff_mac2(acc_s[q][2], acc_c[q][2], a.z, al.z, zh.z, zl.z);
-                ff_mac2(acc_s[q][3], acc_c[q][3], a.w, al.w, zh.w, zl.w);
-            } else {
-                ff_mac1(acc_s[q][0], acc_c[q][0], a.x, zh.x, zl.x);
-                ff_mac1(acc_s[q][1], acc_c[q][1], a.y, zh.y, zl.y);
-                ff_mac1(acc_s[q][2], acc_c[q][2], a.z, zh.z, zl.z);
-                ff_mac1(acc_s[q][3], acc_c[q][3], a.w, zh.w, zl.w);
-            }
-        }
-    }
-}
 
 template <int P>
 __global__ void __launch_bounds__(PassCfg<P>::THREADS, RBD_PASS_MINB) pass_kernel(PassParams p) {
@@ -198,6 +157,26 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, RBD_PASS_MINB) pass_kerne
     double best_e = -1.0;
     int64_t best_j = INT64_MAX;
     bool ok = true;
+    FlushCtx fc;
+    fc.T = p.T;
+    fc.ldt = p.ldt;
+    fc.e = p.e;
+    fc.n = p.n;
+    fc.k = k;
+    fc.piv = piv;
+    fc.inv_nu = inv_nu;
+    fc.gcnt = p.gcnt;
+    fc.gslot = p.gslot;
+    fc.gsum = p.gsum;
+    fc.KMAX = p.KMAX;
+    fc.W = p.W;
+    fc.NT = NT;
+    fc.G = G;
+    fc.b = b;
+    fc.L0 = L0;
+    fc.L1 = L1;
+    fc.grp_e = grp_e;
+    fc.flag = flag;
     double e_old[CPW];          // e_j of this warp's columns, prefetched when a group starts
 #pragma unroll
     for (int q = 0; q < CPW; ++q) e_old[q] = 0.0;
@@ -246,80 +225,7 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, RBD_PASS_MINB) pass_kerne
 
         if (t != NT - 1 && u != L1 - 1) continue;
 
-        // ---- end of this CTA's share of column group g: reduce and finalise ----
-        // The four accumulators and the 32 lanes are combined in float-float arithmetic on the
-        // FP32 pipe (fixed order); only lane 0 converts the result to FP64.
-        double tot[CPW];
-#pragma unroll
-        for (int q = 0; q < CPW; ++q) {
-            float sq = acc_s[q][0], cq = acc_c[q][0];
-#pragma unroll
-            for (int e = 1; e < 4; ++e) ff_add(sq, cq, acc_s[q][e], acc_c[q][e]);
-            warp_sum_ff(sq, cq);
-            tot[q] = ff_to_double(sq, cq);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc_s[q][e] = acc_c[q][e] = 0.f;
-        }
-        const bool whole = (g * NT >= L0) && ((g + 1) * NT <= L1);
-        if (!whole) {
-            const int64_t bfirst = unit_owner(g * NT, p.W, G);
-            const int64_t blast = unit_owner(g * NT + NT - 1, p.W, G);
-            const uint32_t ncontrib = (uint32_t)(blast - bfirst + 1);
-            const int64_t slot = b - bfirst;
-            if (lane == 0) {
-#pragma unroll
-                for (int q = 0; q < CPW; ++q) {
-                    const int cw = warp * CPW + q;
-                    if (cw < ncols) p.gslot[(g * p.KMAX + slot) * C + cw] = tot[q];
-                }
-                __threadfence();
-            }
-            named_bar(1, NCONS);
-            if (tid == 0) *flag = (atomicAdd(&p.gcnt[g], 1u) == ncontrib - 1);
-            named_bar(1, NCONS);
-            if (!*flag) continue;
-            __threadfence();
-            if (lane == 0) {
-#pragma unroll
-                for (int q = 0; q < CPW; ++q) {
-                    const int cw = warp * CPW + q;
-                    if (cw < ncols) {
-                        double acc = 0.0;
-                        for (uint32_t sl = 0; sl < ncontrib; ++sl)
-                            acc += __ldcg(&p.gslot[(g * p.KMAX + sl) * C + cw]);
-                        tot[q] = acc;
-                    }
-                }
-            }
-            if (tid == 0) p.gcnt[g] = 0;
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < CPW; ++q) {
-                const int cw = warp * CPW + q;
-                if (cw < ncols) {
-                    const int64_t j = c0 + cw;
-                    const double cj = tot[q] * inv_nu;
-                    p.T[j * p.ldt + k] = cj;
-                    const double en = (j == piv) ? 0.0 : fmax(e_old[q] - cj * cj, 0.0);
-                    p.e[j] = en;
-                    grp_e[gbuf * C + cw] = en;
-                    if (better(en, j, best_e, best_j)) {
-                        best_e = en;
-                        best_j = j;
-                    }
-                }
-            }
-        }
-        // one barrier per group: thread 0 sums this buffer while the other warps move on; the
-        // buffer is written again two groups later, after thread 0 has passed the next barrier
-        named_bar(1, NCONS);
-        if (tid == 0) {
-            double sacc = 0.0;
-            for (int cw = 0; cw < ncols; ++cw) sacc += grp_e[gbuf * C + cw];
-            p.gsum[g] = sacc;
-        }
-        gbuf ^= 1;
+        flush_group<CPW, C, NCONS>(fc, g, warp, lane, tid, acc_s, acc_c, e_old, best_e, best_j, gbuf);
     }
 
     // ---- per-CTA argmax candidate, then the grid-level last arriver ----

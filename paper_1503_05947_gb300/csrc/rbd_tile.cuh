@@ -1,0 +1,156 @@
+// rbd_tile.cuh -- the fused pass's per-tile arithmetic and per-column-group finalisation,
+// shared by the stepwise pass kernel (rbd_pass.cu) and the persistent loop kernel (rbd_loop.cu).
+//
+//   c_j = xi_k' X(:, j)   (step 2.2, T(k, j) = c_j)
+//   e_j <- e_j - c_j^2    (Eq. (evalerr) with A = I and orthonormal Y: ||x||^2 - ||c||^2)
+//   argmax_j e_j          (step 2.3; lowest j on ties)
+#pragma once
+
+#include "rbd_device.cuh"
+
+namespace rbd {
+
+// CTA that processes unit u when W units are split into G contiguous ranges
+// [floor(b W / G), floor((b + 1) W / G)).
+__device__ __forceinline__ int64_t unit_owner(int64_t u, int64_t W, int64_t G) {
+    return ((u + 1) * G + W - 1) / W - 1;
+}
+
+// Float-float dot-product contributions of one staged tile for this warp's CPW columns.
+// Stage layout: [xi hi (rows) | xi lo (rows) | pad to 2*MT | column c plane p at (c*P + p)*rows].
+// FULL tiles (rows == MT) compile to straight-line code; the ragged last row tile of a column
+// group takes the generic path.
+template <int P, int CPW, int MT, bool FULL>
+__device__ __forceinline__ void consume_tile(const float* __restrict__ st, int rows, int warp, int lane,
+                                             float (&acc_s)[CPW][4], float (&acc_c)[CPW][4]) {
+    constexpr int XI = 2 * MT;
+    const int R = FULL ? MT : rows;
+    const int nsl = FULL ? MT / 128 : (rows >> 7);
+#pragma unroll
+    for (int sl = 0; sl < MT / 128; ++sl) {
+        if (!FULL && sl >= nsl) break;
+        const int off = sl * 128 + lane * 4;
+        const float4 zh = *reinterpret_cast<const float4*>(st + off);
+        const float4 zl = *reinterpret_cast<const float4*>(st + R + off);
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+            const float* col = st + XI + (warp * CPW + q) * P * R + off;
+            const float4 a = *reinterpret_cast<const float4*>(col);
+            if (P == 2) {
+                const float4 al = *reinterpret_cast<const float4*>(col + R);
+                ff_mac2(acc_s[q][0], acc_c[q][0], a.x, al.x, zh.x, zl.x);
+                ff_mac2(acc_s[q][1], acc_c[q][1], a.y, al.y, zh.y, zl.y);
+                ff_mac2(acc_s[q][2], acc_c[q][2], a.z, al.z, zh.z, zl.z);
+                ff_mac2(acc_s[q][3], acc_c[q][3], a.w, al.w, zh.w, zl.w);
+            } else {
+                ff_mac1(acc_s[q][0], acc_c[q][0], a.x, zh.x, zl.x);
+                ff_mac1(acc_s[q][1], acc_c[q][1], a.y, zh.y, zl.y);
+                ff_mac1(acc_s[q][2], acc_c[q][2], a.z, zh.z, zl.z);
+                ff_mac1(acc_s[q][3], acc_c[q][3], a.w, zh.w, zl.w);
+            }
+        }
+    }
+}
+
+// Everything the end-of-group finalisation needs.
+struct FlushCtx {
+    double* T;
+    int64_t ldt;
+    double* e;
+    int64_t n;
+    int64_t k;          // row of T being written (basis index)
+    int64_t piv;        // column whose basis this is: its residual is set to 0
+    double inv_nu;      // dot products were taken with v2; xi_k = v2 / nu
+    uint32_t* gcnt;     // per-group arrival counters (zero at rest)
+    double* gslot;      // per-group partial sums (ngroups x KMAX x C)
+    double* gsum;       // per-group sums of e_j
+    int KMAX;
+    int64_t W, NT, G, b, L0, L1;
+    double* grp_e;      // shared: 2 x C (double buffer)
+    int* flag;          // shared
+};
+
+// End of this CTA's share of column group g: combine the accumulators (float-float, fixed
+// order), publish or combine partials of a group split between CTAs (the last CTA to arrive
+// sums them in CTA order), and finalise the group's columns: T(k, j), e_j, the running argmax
+// (best_e, best_j) and the group sum of e_j.  Called by all consumer threads (NCONS).
+template <int CPW, int C, int NCONS>
+__device__ __forceinline__ void flush_group(const FlushCtx& f, int64_t g, int warp, int lane, int tid,
+                                            float (&acc_s)[CPW][4], float (&acc_c)[CPW][4],
+                                            const double (&e_old)[CPW], double& best_e, int64_t& best_j,
+                                            int& gbuf) {
+    const int64_t c0 = g * C;
+    const int ncols = (int)min((int64_t)C, f.n - c0);
+    double tot[CPW];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+        float sq = acc_s[q][0], cq = acc_c[q][0];
+#pragma unroll
+        for (int e = 1; e < 4; ++e) ff_add(sq, cq, acc_s[q][e], acc_c[q][e]);
+        warp_sum_ff(sq, cq);
+        tot[q] = ff_to_double(sq, cq);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc_s[q][e] = acc_c[q][e] = 0.f;
+    }
+    const bool whole = (g * f.NT >= f.L0) && ((g + 1) * f.NT <= f.L1);
+    if (!whole) {
+        const int64_t bfirst = unit_owner(g * f.NT, f.W, f.G);
+        const int64_t blast = unit_owner(g * f.NT + f.NT - 1, f.W, f.G);
+        const uint32_t ncontrib = (uint32_t)(blast - bfirst + 1);
+        const int64_t slot = f.b - bfirst;
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < CPW; ++q) {
+                const int cw = warp * CPW + q;
+                if (cw < ncols) f.gslot[(g * f.KMAX + slot) * C + cw] = tot[q];
+            }
+            __threadfence();
+        }
+        named_bar(1, NCONS);
+        if (tid == 0) *f.flag = (atomicAdd(&f.gcnt[g], 1u) == ncontrib - 1);
+        named_bar(1, NCONS);
+        if (!*f.flag) return;
+        __threadfence();
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < CPW; ++q) {
+                const int cw = warp * CPW + q;
+                if (cw < ncols) {
+                    double acc = 0.0;
+                    for (uint32_t sl = 0; sl < ncontrib; ++sl) acc += __ldcg(&f.gslot[(g * f.KMAX + sl) * C + cw]);
+                    tot[q] = acc;
+                }
+            }
+        }
+        if (tid == 0) f.gcnt[g] = 0;
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+            const int cw = warp * CPW + q;
+            if (cw < ncols) {
+                const int64_t j = c0 + cw;
+                const double cj = tot[q] * f.inv_nu;
+                f.T[j * f.ldt + f.k] = cj;
+                const double en = (j == f.piv) ? 0.0 : fmax(e_old[q] - cj * cj, 0.0);
+                f.e[j] = en;
+                f.grp_e[gbuf * C + cw] = en;
+                if (better(en, j, best_e, best_j)) {
+                    best_e = en;
+                    best_j = j;
+                }
+            }
+        }
+    }
+    // one barrier per group: thread 0 sums this buffer while the other warps move on; the
+    // buffer is written again two groups later, after thread 0 has passed the next barrier
+    named_bar(1, NCONS);
+    if (tid == 0) {
+        double sacc = 0.0;
+        for (int cw = 0; cw < ncols; ++cw) sacc += f.grp_e[gbuf * C + cw];
+        f.gsum[g] = sacc;
+    }
+    gbuf ^= 1;
+}
+
+}  // namespace rbd

@@ -86,6 +86,7 @@ struct PassCfgBf16 {
 
 constexpr int kGemvRows = 128;     // rows per CTA of the row-parallel GEMVs
 constexpr int kGemvTargetCtas = 304;
+constexpr int kLoopMaxRows = 512;  // largest row block per CTA of the persistent loop kernel
 
 struct Work {
     // sizes
@@ -104,10 +105,17 @@ struct Work {
     int64_t LC_MAX, RC_MAX;
     int num_sms;
     int evict_first;
+    // persistent loop kernel (use_loop = 1): its grid, row blocks and shared memory
+    int use_loop;
+    int G_loop;             // CTAs (one per SM at most)
+    int R;                  // rows per CTA block (multiple of 4)
+    int LC;                 // Y columns per streamed chunk
+    size_t loop_smem;       // dynamic shared memory bytes
     // regions
     Ctl* ctl;
     void* planes;
-    float *yh, *yl;
+    float *yh, *yl;         // stepwise path: split Y, column-major (ldp x d_max)
+    float* ysb;             // loop path: split Y, row-block-major [G_loop][2][d_max][R]
     double *v1, *v2;
     float *v1h, *v1l, *v2s;
     double *e, *xn2;
@@ -125,8 +133,9 @@ struct Work {
 };
 
 // Fill sizes/geometry of `w` (region offsets in the pointer fields); false on unsupported sizes.
+// loop_max_smem > 0 allows the persistent loop kernel with at most that much shared memory.
 bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms,
-               int pass_ctas_per_sm);
+               int pass_ctas_per_sm, int loop_max_smem);
 // Carve the regions of `w` out of `base` (at least w.total_bytes, 256-byte aligned).
 void carve_work(Work& w, void* base);
 
@@ -145,5 +154,13 @@ cudaError_t launch_project(const double* Y, int64_t m, int64_t d, int64_t ldy, c
 // Dynamic shared-memory opt-in for the pass kernels and their resident CTAs per SM, indexed by
 // storage type (once per device).
 cudaError_t pass_kernel_setup(int ctas_per_sm[3]);
+
+// Persistent loop kernel: shared-memory bytes for a plan (0 if the storage type has no loop
+// kernel), one-time attribute setup, and the cooperative launch of the whole greedy loop.
+size_t loop_smem_bytes(int xt, int R, int LC);
+int loop_chunk_cols_for(int xt, int R);
+cudaError_t loop_kernel_setup(int max_smem);
+cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, double* T, int64_t ldt,
+                        int64_t* pivots, double* err, double* nu_out, cudaStream_t st);
 
 }  // namespace rbd

@@ -42,7 +42,8 @@ class _Result(ctypes.Structure):
 class _Profile(ctypes.Structure):
     _fields_ = [("pass_launches", ctypes.c_int64), ("pass_ms", ctypes.c_double),
                 ("orth_launches", ctypes.c_int64), ("orth_ms", ctypes.c_double), ("init_ms", ctypes.c_double),
-                ("pass_bytes", ctypes.c_int64)]
+                ("pass_bytes", ctypes.c_int64), ("loop_launches", ctypes.c_int64), ("loop_ms", ctypes.c_double),
+                ("loop_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
