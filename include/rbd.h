@@ -149,6 +149,39 @@ rbd_status rbd_compress_host(const void* X, rbd_dtype xt, int64_t m, int64_t n, 
                              int64_t* pivots, double* err, double* nu,
                              void* stream, rbd_result* result);
 
+/* Size of the fixed device workspace of rbd_compress_noalloc (64 MiB per device). */
+#define RBD_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/*
+ * rbd_compress_noalloc -- rbd_compress without any memory allocation.  The paper has no
+ * counterpart: this is a deployment form of Algorithm 1, with the same arguments, layout,
+ * outputs and results as rbd_compress, but its workspace is a fixed array of
+ * RBD_NOALLOC_SCRATCH_BYTES in device memory that belongs to the library (one per device).
+ *
+ * For callers that cannot allocate while they compress: a serving loop that bans allocator
+ * calls on its hot path (device allocation may synchronise the device or grow a memory pool),
+ * a process whose device memory is already held by another caching allocator, or code under
+ * a hard memory cap.  The call allocates nothing: no device memory, no pinned or mapped host
+ * memory, no CUDA events (so rbd_set_profiling has no effect on it).
+ *
+ *  X, xt, m, n, ldx, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err, nu, stream, result
+ *          as for rbd_compress (device pointers; result on the host).
+ *
+ *  The first call on a device, made with that device current, sets the kernels' attributes
+ *  and looks up the array's device address (cudaGetSymbolAddress); make it before any stream
+ *  capture begins.  The call synchronises `stream` at its end, like rbd_compress.
+ *  Calls that overlap on one device (several host threads, or several streams) share the one
+ *  array and race: the caller must serialise them.
+ *  Errors: those of rbd_compress, and RBD_ENOMEM when the workspace these sizes need
+ *  (rbd_compress_workspace_bytes) is larger than RBD_NOALLOC_SCRATCH_BYTES -- for an FP64 X
+ *  roughly m * n <= 7 million elements.
+ */
+rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
+                                double tol, rbd_tol_mode mode, int64_t d_max, int64_t start,
+                                double* Y, int64_t ldy, double* T, int64_t ldt,
+                                int64_t* pivots, double* err, double* nu,
+                                void* stream, rbd_result* result);
+
 /*
  * rbd_project -- the out-of-sample map of Section 3.1, v_C = Y' v, for k vectors at once:
  * C = Y' V.

@@ -10,6 +10,7 @@ from .rbd import (  # noqa: F401
     colmajor_empty,
     compress,
     compress_host,
+    compress_noalloc,
     get_profile,
     load,
     project,

@@ -72,6 +72,9 @@ def load():
     lib.rbd_compress_host.restype = ctypes.c_int
     lib.rbd_compress_host.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
                                       _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.POINTER(_Result)]
+    lib.rbd_compress_noalloc.restype = ctypes.c_int
+    lib.rbd_compress_noalloc.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
+                                         _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.POINTER(_Result)]
     lib.rbd_project.restype = ctypes.c_int
     lib.rbd_project.argtypes = [_PTR, _I64, _I64, _I64, _PTR, ctypes.c_int, _I64, _I64, _PTR, _I64, _PTR]
     lib.rbd_set_profiling.restype = None
@@ -169,6 +172,38 @@ def compress(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: 
                               err.data_ptr(), nu.data_ptr(), ws_ptr, ws_bytes, _stream_ptr(dev),
                               ctypes.byref(res))
     _check(st, "rbd_compress")
+    d = int(res.d)
+    return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
+                      STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),
+                      float(res.x_fro), float(res.x_maxcol), int(res.launches))
+
+
+def compress_noalloc(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: str = "maxcol_abs",
+                     out: Optional[dict] = None) -> Compressed:
+    """rbd_compress_noalloc: ``compress`` with the library's fixed device workspace.  Pass the
+    outputs preallocated in ``out`` (column-major CUDA tensors Y, T and vectors pivots, err, nu
+    on X's device) to keep the whole call free of allocations."""
+    lib = load()
+    if not X.is_cuda:
+        raise ValueError("X must be a CUDA tensor")
+    if X.dtype not in DTYPES:
+        raise ValueError(f"unsupported dtype {X.dtype}")
+    m, n = X.shape
+    ldx = _colmajor(X, "X")
+    dev = X.device
+    if out is None:
+        out = {"Y": colmajor_empty(m, d_max, torch.float64, dev), "T": colmajor_empty(d_max, n, torch.float64, dev),
+               "pivots": torch.empty(d_max, dtype=torch.int64, device=dev),
+               "err": torch.empty(d_max, dtype=torch.float64, device=dev),
+               "nu": torch.empty(d_max, dtype=torch.float64, device=dev)}
+    Y, T, piv, err, nu = out["Y"], out["T"], out["pivots"], out["err"], out["nu"]
+    res = _Result()
+    with torch.cuda.device(dev):
+        st = lib.rbd_compress_noalloc(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, float(tol), TOL_MODES[tol_mode],
+                                      int(d_max), int(start), Y.data_ptr(), _colmajor(Y, "Y"), T.data_ptr(),
+                                      _colmajor(T, "T"), piv.data_ptr(), err.data_ptr(), nu.data_ptr(),
+                                      _stream_ptr(dev), ctypes.byref(res))
+    _check(st, "rbd_compress_noalloc")
     d = int(res.d)
     return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
                       STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),
