@@ -62,9 +62,9 @@ def measured_peaks() -> dict:
 
 
 def ncu_traffic() -> dict | None:
-    """DRAM bytes per pass-kernel launch from the committed ncu summary, if it was taken on
-    the current pass-kernel source."""
-    p = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
+    """DRAM bytes per launch of the persistent loop kernel on this workload, from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "loop_kernel_image8192_f64_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -269,25 +269,28 @@ def run_gpu(args, world, rank, local):
     bytes_per_pass = M * N * 8.0
     value = world * passes_total * bytes_per_pass / t / 1e9
 
-    # end to end through the host-buffer entry point (pinned host X, copies inside the region)
-    Xh = torch.from_numpy(np.ascontiguousarray(q.T)).to(torch.float64).div_(255.0).pin_memory().t()
-    outs = {"Y": torch.empty((D_MAX, M), dtype=torch.float64).pin_memory().t(),
-            "T": torch.empty((N, D_MAX), dtype=torch.float64).pin_memory().t(),
-            "pivots": torch.empty(D_MAX, dtype=torch.int64).pin_memory(),
-            "err": torch.empty(D_MAX, dtype=torch.float64).pin_memory(),
-            "nu": torch.empty(D_MAX, dtype=torch.float64).pin_memory()}
-    rh = rbd.compress_host(Xh, TOL, D_MAX, tol_mode=TOL_MODE, device=dev, out=outs)  # warm-up
-    e2e_steps = max(1, min(args.steps, 5))
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    e2e_passes = 0
-    for _ in range(e2e_steps):
-        rh = rbd.compress_host(Xh, TOL, D_MAX, tol_mode=TOL_MODE, device=dev, out=outs)
-        e2e_passes += rh.d + 1
-    t_e2e = barrier_max(world, time.perf_counter() - t0)
-    e2e_value = world * e2e_passes * bytes_per_pass / t_e2e / 1e9
-    d2h = M * rh.d * 8 + rh.d * N * 8 + rh.d * 8 * 3
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the host-buffer entry point (pinned host X, copies inside the region)
+        Xh = torch.from_numpy(np.ascontiguousarray(q.T)).to(torch.float64).div_(255.0).pin_memory().t()
+        outs = {"Y": torch.empty((D_MAX, M), dtype=torch.float64).pin_memory().t(),
+                "T": torch.empty((N, D_MAX), dtype=torch.float64).pin_memory().t(),
+                "pivots": torch.empty(D_MAX, dtype=torch.int64).pin_memory(),
+                "err": torch.empty(D_MAX, dtype=torch.float64).pin_memory(),
+                "nu": torch.empty(D_MAX, dtype=torch.float64).pin_memory()}
+        rh = rbd.compress_host(Xh, TOL, D_MAX, tol_mode=TOL_MODE, device=dev, out=outs)  # warm-up
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_passes = 0
+        for _ in range(e2e_steps):
+            rh = rbd.compress_host(Xh, TOL, D_MAX, tol_mode=TOL_MODE, device=dev, out=outs)
+            e2e_passes += rh.d + 1
+        t_e2e = barrier_max(world, time.perf_counter() - t0)
+        e2e = {"value": world * e2e_passes * bytes_per_pass / t_e2e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": M * rh.d * 8 + rh.d * N * 8 + rh.d * 8 * 3,
+               "steps": e2e_steps}
 
     peaks = measured_peaks()
     tr = ncu_traffic()
@@ -325,8 +328,7 @@ def run_gpu(args, world, rank, local):
                            "l2": "inputs larger than L2 (X 512 MiB vs 129 MB L2)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": M * N * 8,
-                        "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                "e2e": e2e,
                 "gpu_launches": launches,
                 "breakdown_ms_per_step": {"loop_kernel": loop_ms / args.steps, "stepwise_pass": pass_ms / args.steps,
                                           "stepwise_orth": orth_ms / args.steps, "init": init_ms / args.steps},
@@ -348,8 +350,13 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=12, help="bases in the oracle CPU-baseline sample")
     ap.add_argument("--ref-steps", type=int, default=3, help="bases per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--d-max", type=int, default=512,
+                    help="basis limit; values below 512 give the short profiling case, not a bench line")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (end-to-end) measurement")
     args = ap.parse_args()
     world, rank, local = dist_setup()
+    global D_MAX
+    D_MAX = args.d_max
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
