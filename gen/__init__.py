@@ -11,7 +11,9 @@ from .inputs import (  # noqa: F401
     image_like_factors,
     image_like_u8,
     u8_to_unit_f64,
+    parametric_params,
     parametric_snapshots,
+    parametric_snapshots_torch,
     paper_rank_function,
     paper_approx_function,
     orthogonal_columns,

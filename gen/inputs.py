@@ -115,15 +115,40 @@ def u8_to_unit_f64(q: np.ndarray) -> np.ndarray:
     return np.asfortranarray(q.astype(np.float64) / 255.0)
 
 
-def parametric_snapshots(m: int, n: int, seed: int = 2) -> np.ndarray:
-    """Column j = f(s; mu_j) = 1 / sqrt((s - mu1_j)^2 + mu2_j^2) on s_i = i / (m - 1);
-    mu1 ~ U[-1, -0.01], mu2 ~ U[0.01, 1] (seeded)."""
+def parametric_params(m: int, n: int, seed: int = 2):
+    """Grid and parameters of the parametric snapshot matrix: s_i = i / (m - 1) (m points),
+    mu1 ~ U[-1, -0.01], mu2 ~ U[0.01, 1] (n each, seeded)."""
     rng = np.random.default_rng(seed)
     mu1 = rng.uniform(-1.0, -0.01, n)
     mu2 = rng.uniform(0.01, 1.0, n)
     s = np.arange(m, dtype=np.float64) / max(m - 1, 1)
+    return s, mu1, mu2
+
+
+def parametric_snapshots(m: int, n: int, seed: int = 2) -> np.ndarray:
+    """Column j = f(s; mu_j) = 1 / sqrt((s - mu1_j)^2 + mu2_j^2) on s_i = i / (m - 1);
+    mu1 ~ U[-1, -0.01], mu2 ~ U[0.01, 1] (seeded)."""
+    s, mu1, mu2 = parametric_params(m, n, seed)
     x = 1.0 / np.sqrt((s[:, None] - mu1[None, :]) ** 2 + mu2[None, :] ** 2)
     return np.asfortranarray(x)
+
+
+def parametric_snapshots_torch(m: int, n: int, seed: int = 2, device="cuda", dtype=None):
+    """The same matrix built with torch on `device` (column-major), for sizes too large to build
+    on the host: the same seeded parameters, the same formula evaluated elementwise in FP64,
+    then cast to `dtype` (round to nearest)."""
+    import torch
+    s, mu1, mu2 = parametric_params(m, n, seed)
+    st = torch.from_numpy(s).to(device)
+    m1 = torch.from_numpy(mu1).to(device)
+    m2 = torch.from_numpy(mu2).to(device)
+    xt = torch.empty((n, m), dtype=dtype or torch.float64, device=device)
+    step = max(1, (1 << 27) // max(m, 1))
+    for j0 in range(0, n, step):
+        j1 = min(n, j0 + step)
+        blk = 1.0 / torch.sqrt((st[None, :] - m1[j0:j1, None]) ** 2 + m2[j0:j1, None] ** 2)
+        xt[j0:j1] = blk.to(xt.dtype)
+    return xt.t()
 
 
 def paper_rank_function(npts: int, which: int) -> np.ndarray:

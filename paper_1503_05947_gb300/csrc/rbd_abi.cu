@@ -57,7 +57,7 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     w.G = (int)std::min<int64_t>((int64_t)num_sms * std::max(1, pass_ctas_per_sm), w.W);
     // The persistent loop kernel: one CTA per SM at most, each owning a block of R rows of Y.
     w.use_loop = 0;
-    if (loop_max_smem > 0 && xt != RBD_BF16) {
+    if (loop_max_smem > 0) {
         const int64_t gl = std::min<int64_t>(num_sms, std::max<int64_t>(w.W, ceil_div(w.ldp, kLoopMaxRows)));
         const int64_t R = round_up(ceil_div(w.ldp, gl), 4);
         if (R <= kLoopMaxRows) {
@@ -299,7 +299,7 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
     Work w;
     if (!plan_work(w, m, n, ldx, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem))
         return RBD_EUNSUPPORTED;
-    if (xt == RBD_BF16) return RBD_EUNSUPPORTED;
+    if (xt == RBD_BF16 && !w.use_loop) return RBD_EUNSUPPORTED;  // BF16 runs in the persistent kernel only
 
     bool own = false;
     void* ws = workspace;

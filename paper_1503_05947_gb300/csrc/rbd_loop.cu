@@ -40,7 +40,7 @@ struct LoopParams {
     int64_t m, n, ldp, ldx, ldt, ldy, d_max;
     int xt;
     // X planes (tile-major) and pass geometry
-    const float* planes;
+    const unsigned char* planes;
     int64_t group_stride, tile_stride, NT, ngroups, W;
     int KMAX;
     int evict_first;
@@ -77,18 +77,30 @@ struct LoopSmem {
     size_t bars, v1s, v2own, part, coef, v1split, scratch, total;
 };
 
-// Y columns per streamed chunk: both planes of LC x R floats fill at most one ring stage.
-template <int P>
+// Ring stages per Y-chunk buffer: a chunk of a tall row block spans several stages, so that it
+// still holds about 32 columns of both planes (at most half the ring, so that two chunks are in
+// flight).
+template <int XT>
+__host__ __device__ inline int loop_ybuf_stages(int R) {
+    constexpr int S = TileCfg<XT>::S, STAGE = TileCfg<XT>::STAGE_FLOATS;
+    int spb = (int)((32 * 2 * (int64_t)R + STAGE - 1) / STAGE);
+    if (spb > S / 2) spb = S / 2;
+    if (spb < 1) spb = 1;
+    return spb;
+}
+
+// Y columns per chunk: both planes of LC x R floats fill one Y-chunk buffer.
+template <int XT>
 __host__ __device__ inline int loop_chunk_cols(int R) {
-    int lc = (PassCfg<P>::STAGE_FLOATS / 2) / R;
+    int lc = (loop_ybuf_stages<XT>(R) * TileCfg<XT>::STAGE_FLOATS / 2) / R;
     lc &= ~3;
     if (lc > 256) lc = 256;
     return lc;
 }
 
-template <int P>
+template <int XT>
 __host__ __device__ inline LoopSmem loop_smem_layout(int R, int LC) {
-    using Cfg = PassCfg<P>;
+    using Cfg = TileCfg<XT>;
     LoopSmem s;
     size_t o = (size_t)Cfg::S * Cfg::STAGE_FLOATS * 4;  // the ring: pass stages / Y chunks
     s.bars = o;
@@ -147,8 +159,8 @@ __device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint3
     return *s_ok != 0;
 }
 
-// Streams columns [0, k) of this CTA's Y slice, LC columns at a time, through the NB stage
-// buffers of the pass ring (idle during the orthogonalisation), up to NB chunks in flight.
+// Streams columns [0, k) of this CTA's Y slice, LC columns at a time, through NB buffers made
+// of consecutive stages of the pass ring (idle during the orthogonalisation), up to NB chunks in flight.
 // Bulk copies are issued by consumer thread 0 and complete on ybar[buffer]; body(yh, yl, ch,
 // cl, l0, lc) runs for each chunk with all consumers; load_coef(l, hi, lo) gives the
 // coefficient of column l (staged in shared memory next to the chunk).  np = planes streamed.
@@ -240,16 +252,17 @@ __device__ __forceinline__ void ystream_end_step(YStream& ys) {
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) loop_kernel(LoopParams p) {
-    using Cfg = PassCfg<P>;
+template <int XT>
+__global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParams p) {
+    using Cfg = TileCfg<XT>;
+    constexpr int UB = Cfg::PL * Cfg::ESIZE;  // X bytes per element and column of a unit
     constexpr int NW = Cfg::NW, CPW = Cfg::CPW, C = Cfg::C, MT = Cfg::MT, S = Cfg::S;
     constexpr int XI = Cfg::XI_FLOATS, STAGE = Cfg::STAGE_FLOATS;
     constexpr int NCONS = NW * 32;
     constexpr int MAXRPT = kLoopMaxRows / NCONS;  // rows per consumer thread when R > NCONS
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const LoopSmem L = loop_smem_layout<P>(p.R, p.LC);
+    const LoopSmem L = loop_smem_layout<XT>(p.R, p.LC);
     float* stages = reinterpret_cast<float*>(smem_raw);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bars);
     uint64_t* empty = full + S;
@@ -292,8 +305,8 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) loop_kernel(LoopParams
     uint32_t gen = 0;
     YStream ys;
     ys.ring = stages;
-    ys.buf_floats = STAGE;
-    ys.NB = S;
+    ys.buf_floats = loop_ybuf_stages<XT>(R) * STAGE;
+    ys.NB = S / loop_ybuf_stages<XT>(R);
     ys.ybar = ybar;
     ys.coef = coef;
     ys.ysb_b = p.ysb + b * 2 * p.d_max * (int64_t)R;
@@ -320,7 +333,7 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) loop_kernel(LoopParams
     double fro_prev = ctl->fro_last;
     const int mode = ctl->mode;
     const double eps_r = ctl->eps_r, eps_r22 = ctl->eps_r22, fro_tol = ctl->fro_tol;
-    const float* planes = p.planes;
+    const unsigned char* planes = p.planes;
     const uint64_t pol_x = p.evict_first ? l2_policy_evict_first() : l2_policy_evict_normal();
     const uint64_t pol_xi = l2_policy_evict_normal();
 
@@ -387,23 +400,39 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) loop_kernel(LoopParams
                 ystream<NCONS>(
                     ys, k, 2, tid, ctl, [&](int64_t, float& hi, float& lo) { hi = lo = 0.f; },
                     [&](const float* yh, const float* yl, const float*, const float*, int64_t l0, int lc) {
-                        // four consecutive threads share a column, each summing a quarter of the
-                        // rows; the quarters are combined in float-float inside the quad
-                        const int quad = tid & 3, lq = tid >> 2;
-                        const int rq = (Rb + 3) >> 2;
-                        const int ra = quad * rq, rz = min(Rb, ra + rq);
-                        for (int lb = 0; lb < lc; lb += NCONS / 4) {
-                            const int l = lb + lq;
-                            float s = 0.f, c = 0.f;
-                            if (l < lc)
-                                for (int r = ra; r < rz; ++r) ff_mac2(s, c, yh[l * R + r], yl[l * R + r], v1h[r], v1l[r]);
-#pragma unroll
-                            for (int o = 1; o < 4; o <<= 1) {
-                                const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-                                const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-                                ff_add(s, c, s2, c2);
+                        // tpc consecutive threads share a column, each summing every tpc-th row in
+                        // two interleaved chains; the parts are combined in float-float inside the
+                        // group of lanes.  tpc (a power of two <= 32) minimises rounds x (rows per
+                        // thread + combine steps).
+                        int tpc = 1, best = 1 << 30;
+                        for (int tq = 1, lg = 0; tq <= 32; tq <<= 1, ++lg) {
+                            const int cost = ((lc + NCONS / tq - 1) / (NCONS / tq)) * ((Rb + tq - 1) / tq + 2 * lg);
+                            if (cost < best) {
+                                best = cost;
+                                tpc = tq;
                             }
-                            if (l < lc && quad == 0) p.hpart[b * p.d_max + l0 + l] = ff_to_double(s, c);
+                        }
+                        const int per = NCONS / tpc;
+                        for (int lb = 0; lb < lc; lb += per) {
+                            const int l = lb + tid / tpc, qq = tid % tpc;
+                            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+                            if (l < lc) {
+                                const float* ch = yh + l * R;
+                                const float* cl = yl + l * R;
+                                int r = qq;
+                                for (; r + tpc < Rb; r += 2 * tpc) {
+                                    ff_mac2(s0, c0, ch[r], cl[r], v1h[r], v1l[r]);
+                                    ff_mac2(s1, c1, ch[r + tpc], cl[r + tpc], v1h[r + tpc], v1l[r + tpc]);
+                                }
+                                if (r < Rb) ff_mac2(s0, c0, ch[r], cl[r], v1h[r], v1l[r]);
+                                ff_add(s0, c0, s1, c1);
+                            }
+                            for (int o = 1; o < tpc; o <<= 1) {
+                                const float s2 = __shfl_xor_sync(0xffffffffu, s0, o);
+                                const float c2 = __shfl_xor_sync(0xffffffffu, c0, o);
+                                ff_add(s0, c0, s2, c2);
+                            }
+                            if (l < lc && qq == 0) p.hpart[b * p.d_max + l0 + l] = ff_to_double(s0, c0);
                         }
                     });
             }
@@ -503,10 +532,11 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) loop_kernel(LoopParams
                         break;
                     }
                     const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
-                    const uint32_t x_bytes = (uint32_t)(C * P) * rows * 4u;
+                    const uint32_t x_bytes = (uint32_t)(C * UB) * rows;
                     float* st = stages + (size_t)ps * STAGE;
                     mbar_arrive_expect_tx(&full[ps], x_bytes);
-                    bulk_g2s(st + XI, planes + g * p.group_stride + t * p.tile_stride, x_bytes, &full[ps], pol_x);
+                    bulk_g2s(st + XI, planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE, x_bytes, &full[ps],
+                             pol_x);
                     if (++ps == S) {
                         ps = 0;
                         pph ^= 1u;
@@ -596,10 +626,11 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) loop_kernel(LoopParams
                     }
                     const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
                     const uint32_t xi_bytes = 2u * rows * 4u;
-                    const uint32_t x_bytes = (uint32_t)(C * P) * rows * 4u;
+                    const uint32_t x_bytes = (uint32_t)(C * UB) * rows;
                     float* st = stages + (size_t)ps * STAGE;
                     mbar_arrive_expect_tx(&full[ps], x_bytes);
-                    bulk_g2s(st + XI, planes + g * p.group_stride + t * p.tile_stride, x_bytes, &full[ps], pol_x);
+                    bulk_g2s(st + XI, planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE, x_bytes, &full[ps],
+                             pol_x);
                     mbar_arrive_expect_tx(&full[ps], xi_bytes);
                     bulk_g2s(st, p.v2s + t * 2 * MT, xi_bytes, &full[ps], pol_xi);
                     if (++ps == S) {
@@ -676,10 +707,17 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) loop_kernel(LoopParams
                 const int rows = (int)min((int64_t)MT, p.ldp - t * MT);
                 if (ok) {
                     const float* st = stages + (size_t)s * STAGE;
-                    if (rows == MT)
-                        consume_tile<P, CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
-                    else
-                        consume_tile<P, CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c);
+                        if constexpr (XT == 2) {
+                        if (rows == MT)
+                            consume_tile_bf16<CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
+                        else
+                            consume_tile_bf16<CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c);
+                    } else {
+                        if (rows == MT)
+                            consume_tile<Cfg::PL, CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
+                        else
+                            consume_tile<Cfg::PL, CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
@@ -781,21 +819,25 @@ __global__ void __launch_bounds__(PassCfg<P>::THREADS, 1) loop_kernel(LoopParams
 }
 
 int loop_chunk_cols_for(int xt, int R) {
-    if (xt == 0) return loop_chunk_cols<2>(R);
+    if (xt == 0) return loop_chunk_cols<0>(R);
     if (xt == 1) return loop_chunk_cols<1>(R);
+    if (xt == 2) return loop_chunk_cols<2>(R);
     return 0;
 }
 
 size_t loop_smem_bytes(int xt, int R, int LC) {
-    if (xt == 0) return loop_smem_layout<2>(R, LC).total;
+    if (xt == 0) return loop_smem_layout<0>(R, LC).total;
     if (xt == 1) return loop_smem_layout<1>(R, LC).total;
+    if (xt == 2) return loop_smem_layout<2>(R, LC).total;
     return 0;
 }
 
 cudaError_t loop_kernel_setup(int max_smem) {
-    cudaError_t e = cudaFuncSetAttribute(loop_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    cudaError_t e = cudaFuncSetAttribute(loop_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(loop_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(loop_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     return e;
 }
 
@@ -810,7 +852,7 @@ cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, do
     p.ldy = ldy;
     p.d_max = w.d_max;
     p.xt = w.xt;
-    p.planes = static_cast<const float*>(w.planes);
+    p.planes = static_cast<const unsigned char*>(w.planes);
     p.group_stride = w.group_stride;
     p.tile_stride = w.tile_stride;
     p.NT = w.NT;
@@ -841,8 +883,10 @@ cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, do
     p.R = w.R;
     p.LC = w.LC;
     void* args[] = {&p};
-    const void* fn = (w.xt == 0) ? (const void*)loop_kernel<2> : (const void*)loop_kernel<1>;
-    const int threads = (w.xt == 0) ? PassCfg<2>::THREADS : PassCfg<1>::THREADS;
+    const void* fn = (w.xt == 0)   ? (const void*)loop_kernel<0>
+                     : (w.xt == 1) ? (const void*)loop_kernel<1>
+                                   : (const void*)loop_kernel<2>;
+    const int threads = (w.xt == 0) ? TileCfg<0>::THREADS : (w.xt == 1) ? TileCfg<1>::THREADS : TileCfg<2>::THREADS;
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)w.G_loop), dim3((unsigned)threads), args, w.loop_smem, st);
 }
 

@@ -121,7 +121,7 @@ extern "C" rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t 
     Work w;
     if (!plan_work(w, m, n, ldx, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem))
         return RBD_EUNSUPPORTED;
-    if (xt == RBD_BF16) return RBD_EUNSUPPORTED;
+    if (xt == RBD_BF16 && !w.use_loop) return RBD_EUNSUPPORTED;
     // the problem's workspace must fit the fixed array
     if (w.total_bytes > (size_t)RBD_NOALLOC_SCRATCH_BYTES) return RBD_ENOMEM;
     carve_work(w, ds.scratch);

@@ -52,6 +52,43 @@ __device__ __forceinline__ void consume_tile(const float* __restrict__ st, int r
     }
 }
 
+// BF16 storage (the precision form): FP32 products of the exact BF16 values with the leading
+// FP32 part of the pivot vector, summed in FP32 over the unit's rows (16 per lane) and folded into
+// the float-float accumulator once per unit.  Stage layout as above with BF16 columns.
+template <int CPW, int MT, bool FULL>
+__device__ __forceinline__ void consume_tile_bf16(const float* __restrict__ st, int rows, int warp, int lane,
+                                                  float (&acc_s)[CPW][4], float (&acc_c)[CPW][4]) {
+    constexpr int XI = 2 * MT;
+    const int R = FULL ? MT : rows;
+    const int nsl = FULL ? MT / 128 : (rows >> 7);
+    const unsigned short* xb = reinterpret_cast<const unsigned short*>(st + XI);
+    float part[CPW][4];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) part[q][e] = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < MT / 128; ++sl) {
+        if (!FULL && sl >= nsl) break;
+        const int off = sl * 128 + lane * 4;
+        const float4 zh = *reinterpret_cast<const float4*>(st + off);
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+            // four consecutive BF16 values; a BF16 value is the upper half of its FP32 pattern
+            const uint2 u = *reinterpret_cast<const uint2*>(xb + (warp * CPW + q) * R + off);
+            part[q][0] = __fmaf_rn(__uint_as_float(u.x << 16), zh.x, part[q][0]);
+            part[q][1] = __fmaf_rn(__uint_as_float(u.x & 0xffff0000u), zh.y, part[q][1]);
+            part[q][2] = __fmaf_rn(__uint_as_float(u.y << 16), zh.z, part[q][2]);
+            part[q][3] = __fmaf_rn(__uint_as_float(u.y & 0xffff0000u), zh.w, part[q][3]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+        const float sum = __fadd_rn(__fadd_rn(part[q][0], part[q][1]), __fadd_rn(part[q][2], part[q][3]));
+        ff_add(acc_s[q][0], acc_c[q][0], sum, 0.f);
+    }
+}
+
 // Everything the end-of-group finalisation needs.
 struct FlushCtx {
     double* T;

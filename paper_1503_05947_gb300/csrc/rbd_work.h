@@ -84,6 +84,31 @@ struct PassCfgBf16 {
     static constexpr size_t SMEM = (size_t)S * STAGE_BYTES + 2 * S * 8 + SCRATCH;
 };
 
+// Tile configuration of the persistent loop kernel's fused pass per storage type of X
+// (0: FP64 as two FP32 planes, 1: FP32, 2: BF16).  PL = planes, ESIZE = bytes per plane element.
+template <int XT>
+struct TileCfg;
+template <>
+struct TileCfg<0> : PassCfg<2> {
+    static constexpr int PL = 2, ESIZE = 4;
+};
+template <>
+struct TileCfg<1> : PassCfg<1> {
+    static constexpr int PL = 1, ESIZE = 4;
+};
+template <>
+struct TileCfg<2> {
+    static constexpr int NW = PassCfgBf16::NW;
+    static constexpr int CPW = PassCfgBf16::CPW;
+    static constexpr int C = PassCfgBf16::C;
+    static constexpr int MT = PassCfgBf16::MT;
+    static constexpr int S = PassCfgBf16::S;
+    static constexpr int XI_FLOATS = PassCfgBf16::XI_FLOATS;
+    static constexpr int STAGE_FLOATS = PassCfgBf16::STAGE_BYTES / 4;
+    static constexpr int THREADS = PassCfgBf16::THREADS;
+    static constexpr int PL = 1, ESIZE = 2;
+};
+
 constexpr int kGemvRows = 128;     // rows per CTA of the row-parallel GEMVs
 constexpr int kGemvTargetCtas = 304;
 constexpr int kLoopMaxRows = 512;  // largest row block per CTA of the persistent loop kernel
