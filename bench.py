@@ -310,6 +310,10 @@ def run_gpu(args, world, rank, local):
             "kernel": kname, "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_per_launch,
             "avg_launch_ms": kern_s * 1e3}
 
+    forms = {}
+    if rank == 0 and not args.no_forms:
+        forms["precision"] = precision_forms(dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         X64 = gen_x64(q)
@@ -330,10 +334,69 @@ def run_gpu(args, world, rank, local):
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e,
                 "gpu_launches": launches,
+                "forms": forms,
                 "breakdown_ms_per_step": {"loop_kernel": loop_ms / args.steps, "stepwise_pass": pass_ms / args.steps,
                                           "stepwise_orth": orth_ms / args.steps, "init": init_ms / args.steps},
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
+
+
+PREC_M, PREC_N, PREC_DMAX = 65536, 16384, 256
+PREC_WORKLOAD = ("parametric snapshots 65536x16384, X_ij = 1/sqrt((s_i - mu1_j)^2 + mu2_j^2), s uniform on [0, 1], "
+                 "mu1 ~ U[-1,-0.01], mu2 ~ U[0.01,1] (seed 2); d_max 256, relative Frobenius tolerance")
+
+
+def precision_forms(dev) -> dict:
+    """The precision form: the same matrix stored in FP64, FP32 and BF16, each compressed to a
+    relative Frobenius tolerance (1e-6 for FP64 and FP32; 1e-2 for BF16, whose storage alone
+    carries ~2^-9 relative error).  Time of the whole rbd_compress call (CUDA events, inputs
+    resident, after one warm-up call), time per pass over X of the persistent kernel, and the
+    relative reconstruction error against the FP64 matrix."""
+    import torch
+
+    import gen
+    import paper_1503_05947_gb300 as rbd
+    X64 = gen.parametric_snapshots_torch(PREC_M, PREC_N, device=dev)
+    x64n = X64.norm().item()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def one(X, tol):
+        rbd.compress(X, tol, PREC_DMAX, tol_mode="fro_rel")
+        rbd.set_profiling(True)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        r = rbd.compress(X, tol, PREC_DMAX, tol_mode="fro_rel")
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        pf = rbd.get_profile()
+        rbd.set_profiling(False)
+        ms = ev0.elapsed_time(ev1)
+        err2 = 0.0
+        for j0 in range(0, PREC_N, 2048):
+            blk = X64[:, j0:j0 + 2048] - r.Y @ r.T[:, j0:j0 + 2048]
+            err2 += float(blk.norm()) ** 2
+        pass_us = 1e3 * pf["loop_ms"] / max(r.d, 1) if pf["loop_kernel"] else 1e3 * pf["pass_ms"] / max(r.d, 1)
+        xbytes = PREC_M * PREC_N * X.element_size()
+        return {"tol": tol, "bases": r.d, "stop_reason": r.stop_reason, "ms": ms, "pass_us": pass_us,
+                "pass_gbs": xbytes / (pass_us * 1e-6) / 1e9, "rel_err_vs_f64": (err2 ** 0.5) / x64n,
+                "x_bytes": xbytes}
+
+    out = {"workload": PREC_WORKLOAD, "timing": "whole rbd_compress call, CUDA events, inputs resident in HBM"}
+    out["f64"] = one(X64, 1e-6)
+    X32 = X64.t().contiguous().to(torch.float32).t()
+    out["f32"] = one(X32, 1e-6)
+    del X32
+    Xb = X64.t().contiguous().to(torch.bfloat16).t()
+    out["bf16"] = one(Xb, 1e-2)
+    del Xb
+    for k in ("f32", "bf16"):
+        out[k]["speedup_vs_f64"] = out["f64"]["ms"] / out[k]["ms"]
+        out[k]["pass_speedup_vs_f64"] = out["f64"]["pass_us"] / out[k]["pass_us"]
+    del X64
+    torch.cuda.empty_cache()
+    return out
 
 
 def gen_x64(q):
@@ -353,6 +416,7 @@ def main():
     ap.add_argument("--d-max", type=int, default=512,
                     help="basis limit; values below 512 give the short profiling case, not a bench line")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (end-to-end) measurement")
+    ap.add_argument("--no-forms", action="store_true", help="skip the precision / batched form measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     global D_MAX

@@ -10,6 +10,7 @@ from .oracle import (  # noqa: F401
     compress,
     project,
     reconstruct,
+    grad,
     TOL_MODES,
     RANK_FLOOR,
 )

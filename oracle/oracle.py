@@ -55,6 +55,9 @@ def load(mutant: int = 0):
                                             ptr, i64, ptr, i64, ptr, ptr, ptr, ptr, ptr, ptr]
         lib.rbd_oracle_project.restype = ctypes.c_int
         lib.rbd_oracle_project.argtypes = [ptr, i64, i64, i64, ptr, i64, i64, ptr, i64]
+        lib.rbd_oracle_grad.restype = ctypes.c_int
+        lib.rbd_oracle_grad.argtypes = [ptr, i64, i64, i64, ptr, i64, ptr, i64, ptr, i64, ptr, i64, i64, dbl, dbl,
+                                        ptr, i64, ptr]
         lib.rbd_oracle_reconstruct.restype = ctypes.c_int
         lib.rbd_oracle_reconstruct.argtypes = [ptr, i64, i64, i64, ptr, i64, i64, ptr, i64]
         _libs[mutant] = lib
@@ -126,3 +129,26 @@ def reconstruct(Y, T) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"rbd_oracle_reconstruct failed with status {rc}")
     return Xr
+
+
+def grad(X, Y, T, pivots, Xo=None, w_rec: float = 1.0, w_proj: float = 1.0, mutant: int = 0):
+    """Adjoint of L = w_rec ||X - Y T||_F^2 + w_proj ||Y' Xo||_F^2 for the fixed pivot set
+    (closed form of rbd_oracle_grad).  Returns (G, loss)."""
+    lib = load(mutant)
+    X = _f64_colmajor(X)
+    m, n = X.shape
+    piv = np.ascontiguousarray(np.asarray(pivots, dtype=np.int64).reshape(-1))
+    d = piv.size
+    Y = _f64_colmajor(np.asarray(Y, dtype=np.float64).reshape(m, d)) if d > 0 else np.zeros((m, 1), order="F")
+    T = _f64_colmajor(np.asarray(T, dtype=np.float64).reshape(d, n)) if d > 0 else np.zeros((1, n), order="F")
+    if Xo is None:
+        Xo = np.zeros((m, 0), order="F")
+    Xo = _f64_colmajor(Xo)
+    k = Xo.shape[1]
+    G = np.zeros((m, n), dtype=np.float64, order="F")
+    loss = np.zeros(1)
+    rc = lib.rbd_oracle_grad(_p(X), m, n, m, _p(Y), m, _p(T), max(d, 1), _p(piv) if d > 0 else None, d,
+                             _p(Xo) if k > 0 else None, k, m, float(w_rec), float(w_proj), _p(G), m, _p(loss))
+    if rc != 0:
+        raise ValueError(f"rbd_oracle_grad failed with status {rc}")
+    return G, float(loss[0])

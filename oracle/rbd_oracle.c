@@ -197,6 +197,89 @@ int rbd_oracle_project(const double* Y, int64_t m, int64_t d, int64_t ldy, const
     return ORC_OK;
 }
 
+/*
+ * Adjoint of the differentiation form (not in the paper): for the FIXED pivot set P of a
+ * compression, with A = X(:, P) = Y R (Gram-Schmidt in pivot order: Y = Q, R = T(:, P) upper
+ * triangular) and T = Y' X,
+ *     L(X) = w_rec ||X - Y T||_F^2 + w_proj ||Y' Xo||_F^2      (Xo fixed out-of-sample data).
+ * Writing P_A = A A^+ (the orthogonal projector onto span A), L = w_rec tr(X'(I - P_A)X) +
+ * w_proj tr(Xo' P_A Xo), and the projector derivative dP_A = (I - P_A) dA A^+ + (A^+)' dA' (I - P_A)
+ * with A^+ = R^-1 Y' give
+ *     dL/dX          = 2 w_rec E,                                   E = X - Y T,
+ *     dL/dX(:, P)   += [-2 w_rec E T' + 2 w_proj (Xo - Y C) C'] R^-T, C = Y' Xo.
+ * Steps in this order: E; C; Z = -2 w_rec E T' + 2 w_proj (Xo - Y C) C' (m x d); W = Z R^-T by
+ * back substitution row by row (W R' = Z, R upper triangular); G = 2 w_rec E; G(:, P(l)) += W(:, l);
+ * loss = w_rec ||E||_F^2 + w_proj ||C||_F^2.  Plain FP64 loops.
+ */
+int rbd_oracle_grad(const double* X, int64_t m, int64_t n, int64_t ldx, const double* Y, int64_t ldy,
+                    const double* T, int64_t ldt, const int64_t* piv, int64_t d, const double* Xo, int64_t k,
+                    int64_t ldxo, double w_rec, double w_proj, double* G, int64_t ldg, double* loss) {
+    if (!X || !Y || !T || !G || !loss || m < 1 || n < 1 || d < 0 || d > n || d > m || k < 0) return ORC_EINVAL;
+    if (ldx < m || ldy < m || ldt < (d > 0 ? d : 1) || ldg < m || (k > 0 && (!Xo || ldxo < m))) return ORC_EINVAL;
+    if (d > 0 && !piv) return ORC_EINVAL;
+    double* E = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    double* C = (double*)malloc(sizeof(double) * (size_t)(d > 0 ? d : 1) * (size_t)(k > 0 ? k : 1));
+    double* Z = (double*)malloc(sizeof(double) * (size_t)m * (size_t)(d > 0 ? d : 1));
+    if (!E || !C || !Z) {
+        free(E);
+        free(C);
+        free(Z);
+        return ORC_ENOMEM;
+    }
+    /* E = X - Y T */
+    double e2 = 0.0;
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t r = 0; r < m; ++r) {
+            double v = X[j * ldx + r];
+            for (int64_t l = 0; l < d; ++l) v -= Y[l * ldy + r] * T[j * ldt + l];
+            E[j * m + r] = v;
+            e2 += v * v;
+        }
+    /* C = Y' Xo */
+    double c2 = 0.0;
+    for (int64_t q = 0; q < k; ++q)
+        for (int64_t l = 0; l < d; ++l) {
+            double v = dot(Y + l * ldy, Xo + q * ldxo, m);
+            C[q * d + l] = v;
+            c2 += v * v;
+        }
+    /* Z = -2 w_rec E T' + 2 w_proj (Xo - Y C) C' */
+    for (int64_t l = 0; l < d; ++l)
+        for (int64_t r = 0; r < m; ++r) {
+            double a = 0.0;
+            for (int64_t j = 0; j < n; ++j) a += E[j * m + r] * T[j * ldt + l];
+            double b = 0.0;
+            for (int64_t q = 0; q < k; ++q) {
+                double res = Xo[q * ldxo + r];
+                for (int64_t l2 = 0; l2 < d; ++l2) res -= Y[l2 * ldy + r] * C[q * d + l2];
+                b += res * C[q * d + l];
+            }
+            double zr = (RBD_ORACLE_MUTANT == 12) ? (2.0 * w_rec * a + 2.0 * w_proj * b)
+                                                  : (-2.0 * w_rec * a + 2.0 * w_proj * b);
+            Z[l * m + r] = zr;
+        }
+    /* W = Z R^-T: for each row, W R' = Z with R(a, b) = T(a, P(b)) upper triangular */
+    if (RBD_ORACLE_MUTANT != 11) {
+        for (int64_t r = 0; r < m; ++r)
+            for (int64_t a = d - 1; a >= 0; --a) {
+                double v = Z[a * m + r];
+                for (int64_t b = a + 1; b < d; ++b) v -= Z[b * m + r] * T[piv[b] * ldt + a];
+                Z[a * m + r] = v / T[piv[a] * ldt + a];
+            }
+    }
+    /* G = 2 w_rec E, then the pivot columns */
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t r = 0; r < m; ++r) G[j * ldg + r] = 2.0 * w_rec * E[j * m + r];
+    if (RBD_ORACLE_MUTANT != 13)
+        for (int64_t l = 0; l < d; ++l)
+            for (int64_t r = 0; r < m; ++r) G[piv[l] * ldg + r] += Z[l * m + r];
+    *loss = w_rec * e2 + w_proj * c2;
+    free(E);
+    free(C);
+    free(Z);
+    return ORC_OK;
+}
+
 /* Uncompress (Section 3.1): Xr(:, j) = Y T(:, j), summed over bases l = 0..d-1 in order. */
 int rbd_oracle_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy, const double* T,
                            int64_t n, int64_t ldt, double* Xr, int64_t ldx) {
