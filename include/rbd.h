@@ -197,6 +197,35 @@ rbd_status rbd_project(const double* Y, int64_t m, int64_t d, int64_t ldy,
                        const void* V, rbd_dtype vt, int64_t k, int64_t ldv,
                        double* C, int64_t ldc, void* stream);
 
+/*
+ * rbd_grad -- adjoint of the differentiation form (an extension: the paper has no gradient).
+ * For the FIXED pivot set of a compression (Y, T, pivots from rbd_compress: A = X(:, pivots)
+ * = Y R with R = T(:, pivots) upper triangular, T = Y' X) and fixed out-of-sample data Xo,
+ *     L(X) = w_rec ||X - Y T||_F^2 + w_proj ||Y' Xo||_F^2
+ * and its gradient with respect to X,
+ *     G = 2 w_rec E,  G(:, pivots) += [-2 w_rec E T' + 2 w_proj (Xo - Y C) C'] R^-T,
+ * with E = X - Y T and C = Y' Xo (the out-of-sample map of Section 3.1).
+ *
+ *  X       [in]  device, m x n, ldx >= m, storage type xt (the matrix that was compressed).
+ *  Y, T    [in]  device FP64, m x d (ldy >= m) and d x n (ldt >= d), as rbd_compress wrote them.
+ *  pivots  [in]  device, d distinct int64 column indices (rbd_compress's pivots).
+ *  d       [in]  0 <= d <= min(m, n, 256).
+ *  Xo      [in]  device, m x k, ldxo >= m, storage type xt; may be NULL when k = 0.
+ *  w_rec, w_proj [in] weights of the two terms.
+ *  G       [out] device FP64, m x n, ldg >= m; or NULL to evaluate the loss only.
+ *  loss    [out] device, one double: L(X).
+ *  stream  [in]  cudaStream_t as void*.  Stream-ordered; allocates its workspace stream-ordered
+ *                (cudaMallocAsync) and frees it; does not synchronise.
+ *  Errors: RBD_EINVAL for bad sizes, leading dimensions or NULL arguments; RBD_EUNSUPPORTED for
+ *  d > 256; RBD_ENOMEM / RBD_ECUDA on allocation or launch failures.
+ */
+rbd_status rbd_grad(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
+                    const double* Y, int64_t ldy, const double* T, int64_t ldt,
+                    const int64_t* pivots, int64_t d,
+                    const void* Xo, int64_t k, int64_t ldxo,
+                    double w_rec, double w_proj,
+                    double* G, int64_t ldg, double* loss, void* stream);
+
 /* Per-kernel timing of the most recent rbd_compress call on this host thread, taken with
    CUDA events recorded on the call's stream around each launch when profiling is enabled
    (rbd_set_profiling(1)).  Times are in milliseconds. */

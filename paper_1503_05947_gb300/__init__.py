@@ -11,6 +11,7 @@ from .rbd import (  # noqa: F401
     compress,
     compress_host,
     compress_noalloc,
+    grad,
     get_profile,
     load,
     project,
@@ -20,3 +21,4 @@ from .rbd import (  # noqa: F401
     workspace_bytes,
 )
 from .buildlib import build  # noqa: F401
+from .autograd import RBDLoss, rbd_loss  # noqa: F401

@@ -75,6 +75,9 @@ def load():
     lib.rbd_compress_noalloc.restype = ctypes.c_int
     lib.rbd_compress_noalloc.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
                                          _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.POINTER(_Result)]
+    lib.rbd_grad.restype = ctypes.c_int
+    lib.rbd_grad.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _PTR, _I64, _PTR, _I64, _PTR, _I64, _PTR, _I64,
+                             _I64, _DBL, _DBL, _PTR, _I64, _PTR, _PTR]
     lib.rbd_project.restype = ctypes.c_int
     lib.rbd_project.argtypes = [_PTR, _I64, _I64, _I64, _PTR, ctypes.c_int, _I64, _I64, _PTR, _I64, _PTR]
     lib.rbd_set_profiling.restype = None
@@ -237,6 +240,45 @@ def compress_host(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_m
     return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
                       STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),
                       float(res.x_fro), float(res.x_maxcol), int(res.launches))
+
+
+def grad(X: torch.Tensor, Y: torch.Tensor, T: torch.Tensor, pivots: torch.Tensor, Xo: Optional[torch.Tensor] = None,
+         w_rec: float = 1.0, w_proj: float = 1.0, need_grad: bool = True):
+    """rbd_grad: L = w_rec ||X - Y T||_F^2 + w_proj ||Y' Xo||_F^2 for the fixed pivot set of a
+    compression, and (need_grad) its gradient with respect to X.  Returns (G or None, loss) with
+    G an m x n column-major FP64 CUDA tensor and loss a 0-dim FP64 CUDA tensor."""
+    lib = load()
+    if not X.is_cuda or X.dtype not in DTYPES:
+        raise ValueError("X must be a CUDA tensor of a supported dtype")
+    m, n = X.shape
+    ldx = _colmajor(X, "X")
+    d = int(pivots.numel())
+    dev = X.device
+    if d > 0:
+        if Y.dtype != torch.float64 or T.dtype != torch.float64:
+            raise ValueError("Y and T must be float64")
+        ldy, ldt = _colmajor(Y, "Y"), _colmajor(T, "T")
+        piv = pivots.to(device=dev, dtype=torch.int64).contiguous()
+    else:
+        ldy, ldt, piv = m, 1, None
+    k, ldxo, xo_ptr = 0, m, None
+    if Xo is not None and Xo.numel() > 0:
+        if Xo.dtype != X.dtype:
+            raise ValueError("Xo must have the dtype of X")
+        if Xo.dim() == 1:
+            Xo = Xo[:, None]
+        k = Xo.shape[1]
+        ldxo = _colmajor(Xo, "Xo")
+        xo_ptr = Xo.data_ptr()
+    G = colmajor_empty(m, n, torch.float64, dev) if need_grad else None
+    loss = torch.empty((), dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        st = lib.rbd_grad(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, Y.data_ptr() if d > 0 else None, ldy,
+                          T.data_ptr() if d > 0 else None, ldt, piv.data_ptr() if d > 0 else None, d, xo_ptr, k,
+                          ldxo, float(w_rec), float(w_proj), G.data_ptr() if G is not None else None, m,
+                          loss.data_ptr(), _stream_ptr(dev))
+    _check(st, "rbd_grad")
+    return G, loss
 
 
 def project(Y: torch.Tensor, V: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
