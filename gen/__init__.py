@@ -18,4 +18,7 @@ from .inputs import (  # noqa: F401
     paper_approx_function,
     orthogonal_columns,
     out_of_sample,
+    batch_specs,
+    decay_spectrum,
+    lowrank_torch,
 )

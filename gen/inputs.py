@@ -203,3 +203,39 @@ def out_of_sample(m: int, k: int, seed: int) -> np.ndarray:
     """k i.i.d. N(0, 1/m) vectors of length m, column-major m x k."""
     rng = np.random.default_rng(seed)
     return np.asfortranarray(rng.standard_normal((m, k)) / np.sqrt(m))
+
+
+def batch_specs(count: int = 2048, seed: int = 3):
+    """Sizes and parameters of the batched workload: m log-uniform in [256, 4096] and n
+    log-uniform in [64, 2048] (rounded), decay rate r ~ U[0.05, 0.5], tolerance log-uniform in
+    [1e-6, 1e-2] (relative max-column mode), d_max = min(m, n, 512)."""
+    rng = np.random.default_rng(seed)
+    m = np.rint(np.exp(rng.uniform(np.log(256), np.log(4096), count))).astype(np.int64)
+    n = np.rint(np.exp(rng.uniform(np.log(64), np.log(2048), count))).astype(np.int64)
+    r = rng.uniform(0.05, 0.5, count)
+    tol = np.exp(rng.uniform(np.log(1e-6), np.log(1e-2), count))
+    return [{"m": int(m[i]), "n": int(n[i]), "rate": float(r[i]), "tol": float(tol[i]),
+             "d_max": int(min(m[i], n[i], 512)), "seed": seed * 100003 + i} for i in range(count)]
+
+
+def decay_spectrum(rate: float, r_max: int) -> np.ndarray:
+    """s_i = exp(-rate i), i = 0.., truncated where s_i < 1e-9 (at most r_max values)."""
+    r = int(min(r_max, np.floor(np.log(1e9) / rate) + 1))
+    return np.exp(-rate * np.arange(r))
+
+
+def lowrank_torch(m: int, n: int, s: np.ndarray, seed: int, device="cuda", dtype=None):
+    """X = U diag(s) V^T with Haar-distributed U (m x r), V (n x r) built with torch on `device`
+    (QR of seeded Gaussian matrices, signs fixed), cast to `dtype`; column-major."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(int(seed))
+    r = len(s)
+    A = torch.randn(m, r, generator=g, dtype=torch.float64).to(device)
+    B = torch.randn(n, r, generator=g, dtype=torch.float64).to(device)
+    qa, ra = torch.linalg.qr(A)
+    qb, rb = torch.linalg.qr(B)
+    qa = qa * torch.sign(torch.diagonal(ra))[None, :]
+    qb = qb * torch.sign(torch.diagonal(rb))[None, :]
+    st = torch.from_numpy(np.asarray(s, dtype=np.float64)).to(device)
+    X = (qa * st[None, :]) @ qb.t()
+    return X.to(dtype or torch.float64).t().contiguous().t()

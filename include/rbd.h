@@ -198,6 +198,77 @@ rbd_status rbd_project(const double* Y, int64_t m, int64_t d, int64_t ldy,
                        double* C, int64_t ldc, void* stream);
 
 /*
+ * Batched form (an extension: the paper compresses one matrix at a time): many independent
+ * matrices, each with its own sizes, tolerance and outputs, compressed by Algorithm 1 in ONE
+ * persistent launch.  Each CTA takes whole matrices from a queue ordered by decreasing size and
+ * runs their greedy loops to the end; results match rbd_compress on each matrix.
+ *
+ * Limits: every matrix has m <= 4096 rows and d_max <= 512 (larger matrices: rbd_compress);
+ * storage type RBD_F64 or RBD_F32, the same for the whole batch.
+ */
+typedef struct rbd_instance {
+    const void* X;        /* device, m x n column-major, ldx >= m */
+    int64_t m, n, ldx;
+    double tol;           /* epsilon_R, interpreted by `mode` (an rbd_tol_mode) */
+    int32_t mode;
+    int32_t reserved;
+    int64_t d_max;        /* 1 <= d_max <= min(m, n, 512) */
+    int64_t start;        /* 0 <= start < n */
+    double* Y;            /* device outputs as for rbd_compress */
+    int64_t ldy;
+    double* T;
+    int64_t ldt;
+    int64_t* pivots;
+    double* err;
+    double* nu;           /* may be NULL */
+} rbd_instance;
+
+/* Per-matrix summary of a batched run (device memory, written by the kernels). */
+typedef struct rbd_batch_result {
+    int64_t d;
+    int64_t next_pivot;
+    int32_t stop_reason;  /* an rbd_stop_reason */
+    int32_t status;       /* RBD_OK, or RBD_ENONFINITE / RBD_EUNSUPPORTED for this matrix */
+    double err_last;
+    double fro_last;
+    double x_fro;
+    double x_maxcol;
+} rbd_batch_result;
+
+typedef struct rbd_batch_plan_s* rbd_batch_plan;
+
+/* Device workspace a plan needs for this batch (0 if a descriptor is invalid). */
+size_t rbd_batch_workspace_bytes(const rbd_instance* inst, int64_t count, rbd_dtype xt);
+
+/* Validate the batch (host array of `count` descriptors), lay the workspace out (caller-owned,
+   256-byte aligned, at least rbd_batch_workspace_bytes) and upload the descriptor table on
+   `stream` (the call synchronises it).  The plan keeps device pointers only; the descriptors'
+   buffers must stay valid while the plan is used.  Errors: RBD_EINVAL, RBD_EUNSUPPORTED (a matrix
+   beyond the limits), RBD_ENOMEM (workspace too small), RBD_ECUDA. */
+rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst, int64_t count,
+                                 rbd_dtype xt, void* workspace, size_t workspace_bytes,
+                                 void* stream);
+
+/* Run the whole batch: a memset, the initial pass over every matrix and the persistent kernel,
+   all stream-ordered; no host synchronisation and no allocation, so a run can be captured in a
+   CUDA graph and replayed.  results: device array of `count` rbd_batch_result. */
+rbd_status rbd_batch_run(rbd_batch_plan plan, rbd_batch_result* results, void* stream);
+
+/* Autotuner: time the run with each candidate pipeline depth (ring stages of the fused pass and
+   of the Gram-Schmidt streams) on this batch and keep the fastest in the plan.  Synchronises
+   `stream`; the outputs hold the results of the last trial.  *stages_out (may be NULL) receives
+   the choice. */
+rbd_status rbd_batch_tune(rbd_batch_plan plan, rbd_batch_result* results, void* stream,
+                          int32_t* stages_out);
+
+rbd_status rbd_batch_plan_destroy(rbd_batch_plan plan);
+
+/* One-shot convenience: plan (with a stream-ordered workspace allocation), run, copy the
+   results to the HOST array `results`, destroy.  Synchronises `stream`. */
+rbd_status rbd_compress_batched(const rbd_instance* inst, int64_t count, rbd_dtype xt,
+                                rbd_batch_result* results, void* stream);
+
+/*
  * rbd_grad -- adjoint of the differentiation form (an extension: the paper has no gradient).
  * For the FIXED pivot set of a compression (Y, T, pivots from rbd_compress: A = X(:, pivots)
  * = Y R with R = T(:, pivots) upper triangular, T = Y' X) and fixed out-of-sample data Xo,

@@ -4,6 +4,7 @@ The greedy compression X ~ Y T of Algorithm 1 runs in hand-written CUDA kernels 
 behind the C ABI of include/rbd.h (librbd.so); ``rbd`` is its thin Python binding.
 """
 from .rbd import (  # noqa: F401
+    BatchPlan,
     Compressed,
     RbdError,
     as_colmajor,

@@ -1,0 +1,861 @@
+// rbd_batch.cu -- the batched form: many independent matrices, each compressed by Algorithm 1,
+// in one persistent launch.
+//
+// batch_init_kernel  the initial pass over every matrix (Section 3.3's pre-computation with
+//                    A = I): e_j = ||x_j||^2 and the tile-major re-layout of X, one warp per
+//                    column of the whole batch.
+// batch_kernel       one CTA per SM; each CTA takes the next matrix from a queue ordered by
+//                    decreasing size (largest first keeps the tail short) and runs its whole
+//                    greedy loop alone, so no grid-wide synchronisation is needed:
+//                      step 2.1-2.2  v1 = x_i - Y t (t = T(0:k, i)), h = Y' v1, v2 = v1 - Y h
+//                                    (classical Gram-Schmidt twice, float-float), nu = ||v2||,
+//                                    stop tests; xi = v2 / nu -> Y(:, k) and shared memory
+//                      fused pass    T(k, :) = xi' X, e_j <- e_j - T(k, j)^2 (Eq. (evalerr),
+//                                    A = I), argmax
+//                    Y (split FP32 planes, column-major, one copy per matrix) and the X tiles
+//                    stream through one ring of shared-memory stages with bulk (TMA) copies;
+//                    xi stays in shared memory for the whole pass.
+// The arithmetic is the persistent loop kernel's (rbd_loop.cu) with G = 1 CTA per matrix.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/rbd.h"
+#include "rbd_device.cuh"
+#include "rbd_tile.cuh"
+#include "rbd_work.h"
+
+namespace rbd {
+
+namespace {
+
+constexpr int kBC = 16;                      // columns per group
+constexpr int kBCPW = 2;                     // columns per consumer warp
+constexpr int kBNW = kBC / kBCPW;            // consumer warps
+constexpr int kBNCONS = kBNW * 32;
+constexpr int kBThreads = kBNCONS + 32;      // + producer warp
+constexpr int kBMT = 256;                    // rows per tile
+constexpr int kBMaxRows = 4096;              // padded rows per matrix
+constexpr int kBMaxD = 512;
+constexpr int kBQR = kBMaxRows / kBNCONS;    // rows per consumer thread
+constexpr int kBRingBytes = 128 * 1024;
+constexpr int kBMaxLC = 64;                  // Y columns per Gram-Schmidt chunk
+
+template <int P>
+struct BCfg {
+    static constexpr int STAGE_BYTES = kBC * P * kBMT * 4;
+    static constexpr int SMAX = kBRingBytes / STAGE_BYTES;
+};
+
+// Device descriptor of one matrix (built on the host, uploaded by plan_create).
+struct BInst {
+    const void* X;
+    int64_t m, n, ldx, ldp, ngroups, NT;
+    double tol;
+    int32_t mode, pad;
+    int64_t d_max, start;
+    double* Y;
+    int64_t ldy;
+    double* T;
+    int64_t ldt;
+    int64_t* piv;
+    double* err;
+    double* nu;
+    float* planes;   // tile-major, as in rbd_work.h
+    float* ys;       // split Y: [2][d_max][ldp]
+    double* e;
+    double* xn2;
+};
+
+struct BatchParams {
+    const BInst* inst;
+    int64_t count;
+    const int32_t* order;     // claim slot -> matrix
+    const int64_t* colstart;  // padded-column prefix sums (count + 1)
+    uint32_t* queue;          // claim counter (zero before the run)
+    int32_t* status;          // per matrix (zero before the run)
+    rbd_batch_result* res;
+    int S;                    // ring stages used by the pass (<= SMAX)
+};
+
+// ---------------------------------------------------------------- initial pass
+template <int P>
+__global__ void __launch_bounds__(256) batch_init_kernel(BatchParams bp) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = bp.colstart[bp.count];
+    for (int64_t q = gw; q < total; q += nw) {
+        // matrix of padded column q: last i with colstart[i] <= q
+        int64_t lo = 0, hi = bp.count - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (bp.colstart[mid] <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        const BInst& I = bp.inst[lo];
+        const int64_t j = q - bp.colstart[lo];
+        const int64_t g = j / kBC;
+        const int c = (int)(j % kBC);
+        const bool live = j < I.n;
+        float s = 0.f, cc = 0.f;
+        int bad = ST_OK;
+        for (int64_t r0 = 4 * lane; r0 < I.ldp; r0 += 128) {
+            const int64_t t = r0 / kBMT;
+            const int64_t rt = min((int64_t)kBMT, I.ldp - t * kBMT);
+            const int64_t base = g * kBC * P * I.ldp + t * kBC * P * kBMT + (int64_t)c * P * rt + (r0 - t * kBMT);
+            float hv[4], lv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t r = r0 + u;
+                double x = 0.0;
+                if (live && r < I.m) x = (P == 2) ? ((const double*)I.X)[j * I.ldx + r] : (double)((const float*)I.X)[j * I.ldx + r];
+                if (!isfinite(x)) {
+                    bad = ST_ENONFINITE;
+                    x = 0.0;
+                }
+                if (P == 2 && fabs(x) >= 0x1p127 && bad == ST_OK) bad = ST_EUNSUPPORTED;
+                if (P == 2) {
+                    split_double(x, hv[u], lv[u]);
+                    ff_mac2(s, cc, hv[u], lv[u], hv[u], lv[u]);
+                } else {
+                    hv[u] = (float)x;
+                    lv[u] = 0.f;
+                    ff_mac1(s, cc, hv[u], hv[u], 0.f);
+                }
+            }
+            float* ph = I.planes + base;
+            *reinterpret_cast<float4*>(ph) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+            if (P == 2) *reinterpret_cast<float4*>(ph + rt) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        }
+        const double tsum = warp_sum_double(ff_to_double(s, cc));
+        const int anybad = __reduce_max_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            if (live) {
+                I.e[j] = tsum;
+                I.xn2[j] = tsum;
+            }
+            if (anybad != ST_OK) atomicCAS(&bp.status[lo], 0, anybad);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- the per-matrix loop
+template <int P>
+__global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
+    using Cfg = BCfg<P>;
+    constexpr int SMAX = Cfg::SMAX;
+    constexpr int STAGE_F = Cfg::STAGE_BYTES / 4;
+    extern __shared__ __align__(128) unsigned char bsm[];
+    float* ring = reinterpret_cast<float*>(bsm);                               // kBRingBytes
+    uint64_t* full = reinterpret_cast<uint64_t*>(bsm + kBRingBytes);           // SMAX
+    uint64_t* empty = full + SMAX;                                             // SMAX
+    uint64_t* ybar = empty + SMAX;                                             // 2
+    float* vh = reinterpret_cast<float*>(ybar + 2);                            // kBMaxRows
+    float* vl = vh + kBMaxRows;                                                // kBMaxRows
+    double* hacc = reinterpret_cast<double*>(vl + kBMaxRows);                  // kBMaxD
+    float* coef = reinterpret_cast<float*>(hacc + kBMaxD);                     // 2 x 2 x kBMaxLC
+    float* wps = coef + 4 * kBMaxLC;                                           // kBNW x kBMaxLC (ff hi)
+    float* wpc = wps + kBNW * kBMaxLC;                                         // (ff lo)
+    double* red = reinterpret_cast<double*>(wpc + kBNW * kBMaxLC);             // 4 kBNW + 16
+    int64_t* redj = reinterpret_cast<int64_t*>(red + 2 * kBNW);
+    double* bc = red + 4 * kBNW;                                               // broadcasts
+    int* flag = reinterpret_cast<int*>(bc + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int S = bp.S;
+
+    if (tid == 0) {
+        for (int s = 0; s < SMAX; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kBNW);
+        }
+        mbar_init(&ybar[0], 1);
+        mbar_init(&ybar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    bool ok = true;
+    uint32_t ycount = 0;          // Y chunks streamed so far (buffer and parity of each)
+    int ps = 0, cs = 0;           // pass ring: producer / consumer stage and phase
+    uint32_t pph = 0, cph = 0;
+    bool preuse = false;
+    const uint64_t pol_x = l2_policy_evict_first();
+    const uint64_t pol_y = l2_policy_evict_normal();
+
+    for (;;) {
+        if (tid == 0) flag[0] = (int)atomicAdd(bp.queue, 1u);
+        __syncthreads();
+        const int64_t slot = flag[0];
+        __syncthreads();
+        if (slot >= bp.count) break;
+        const int64_t idx = bp.order[slot];
+        const BInst I = bp.inst[idx];
+        const int64_t m = I.m, n = I.n, ldp = I.ldp, dmax = I.d_max, NT = I.NT;
+        const int64_t W = I.ngroups * NT;
+
+        // ---- statistics of the initial pass and the tolerances (fixed order)
+        if (warp == 0) {
+            double sum = 0.0, mx = 0.0;
+            for (int64_t j = lane; j < n; j += 32) {
+                const double v = __ldcg(&I.xn2[j]);
+                sum += v;
+                mx = fmax(mx, v);
+            }
+            sum = warp_sum_double(sum);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            if (lane == 0) {
+                bc[0] = sqrt(sum);
+                bc[1] = sqrt(mx);
+            }
+        }
+        __syncthreads();
+        const double x_fro = bc[0], x_maxcol = bc[1];
+        const int st0 = __ldcg(&bp.status[idx]);
+        double fro_tol = -1.0, eps_r, eps_r22;
+        if (I.mode == MODE_FRO_REL) {
+            fro_tol = I.tol * x_fro;
+            eps_r = -1.0;
+            eps_r22 = I.tol * x_fro / sqrt((double)n);
+        } else {
+            eps_r = (I.mode == MODE_MAXCOL_REL) ? I.tol * x_maxcol : I.tol;
+            eps_r22 = eps_r;
+        }
+        int64_t piv = I.start;
+        double fro_prev = x_fro, err_last = 0.0;
+        int32_t stop = (st0 != ST_OK) ? STOP_BREAK : STOP_NONE;
+        int64_t k = 0;
+        // Y chunk geometry: the ring as two buffers of half its size, both planes per chunk
+        const int LC = (int)min((int64_t)kBMaxLC, (int64_t)(kBRingBytes / 8) / (2 * ldp));
+        const int64_t buf_f = kBRingBytes / 8;  // floats per buffer
+
+        // streams Y columns [0, k) in chunks through the two ring buffers (consumer threads);
+        // stage(l, hi, lo) gives the coefficient of column l, body(yh, yl, ch, cl, l0, lc) runs on
+        // the chunk, post(l0, lc) after the barrier that closes it.  Every barrier is reached by
+        // all consumer threads whatever their waits returned.
+        auto ystream = [&](auto&& stage, auto&& body, auto&& post) {
+            const int64_t nch = ceil_div(k, (int64_t)LC);
+            auto issue = [&](int64_t c) {
+                const int bf = (int)((ycount + (uint32_t)c) & 1u);
+                const int64_t l0 = c * LC;
+                const int lc = (int)min((int64_t)LC, k - l0);
+                const uint32_t bytes = (uint32_t)(lc * ldp * 4);
+                mbar_arrive_expect_tx(&ybar[bf], 2u * bytes);
+                bulk_g2s(ring + bf * buf_f, I.ys + l0 * ldp, bytes, &ybar[bf], pol_y);
+                bulk_g2s(ring + bf * buf_f + (int64_t)LC * ldp, I.ys + (dmax + l0) * ldp, bytes, &ybar[bf], pol_y);
+            };
+            if (tid == 0 && nch > 0) issue(0);
+            for (int64_t c = 0; c < nch; ++c) {
+                // buffer (c + 1) & 1 was read by chunk c - 1, finished at the barrier below
+                if (tid == 0 && c + 1 < nch) issue(c + 1);
+                const int bf = (int)((ycount + (uint32_t)c) & 1u);
+                const int64_t l0 = c * LC;
+                const int lc = (int)min((int64_t)LC, k - l0);
+                float* ch = coef + bf * 2 * kBMaxLC;
+                float* cl = ch + kBMaxLC;
+                for (int l = tid; l < lc; l += kBNCONS) stage(l0 + l, ch[l], cl[l]);
+                named_bar(1, kBNCONS);
+                const uint32_t par = ((ycount + (uint32_t)c) >> 1) & 1u;
+                if (ok && !mbar_wait(&ybar[bf], par)) ok = false;
+                if (ok) body(ring + bf * buf_f, ring + bf * buf_f + (int64_t)LC * ldp, ch, cl, l0, lc);
+                named_bar(1, kBNCONS);
+                post(l0, lc);
+            }
+            ycount += (uint32_t)nch;
+        };
+        auto nopost = [](int64_t, int) {};
+
+        while (stop == STOP_NONE && ok) {
+            if (warp < kBNW) {
+                // ---- O1: v1 = x_i - Y t for all rows (rows tid + kBNCONS q)
+                float as[kBQR], ac[kBQR];
+#pragma unroll
+                for (int q = 0; q < kBQR; ++q) as[q] = ac[q] = 0.f;
+                const double* tcol = I.T + piv * I.ldt;
+                if (k > 0)
+                    ystream([&](int64_t l, float& hi, float& lo) { split_double(__ldcg(&tcol[l]), hi, lo); },
+                            [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
+#pragma unroll
+                                for (int q = 0; q < kBQR; ++q) {
+                                    const int64_t r = tid + (int64_t)kBNCONS * q;
+                                    if (r >= ldp) break;
+                                    for (int l = 0; l < lc; ++l)
+                                        ff_mac2(as[q], ac[q], yh[l * ldp + r], yl[l * ldp + r], ch[l], cl[l]);
+                                }
+                            },
+                            nopost);
+#pragma unroll
+                for (int q = 0; q < kBQR; ++q) {
+                    const int64_t r = tid + (int64_t)kBNCONS * q;
+                    if (r >= ldp) break;
+                    double v = 0.0;
+                    if (r < m) {
+                        const double x = (P == 2) ? ((const double*)I.X)[piv * I.ldx + r]
+                                                  : (double)((const float*)I.X)[piv * I.ldx + r];
+                        v = x - ff_to_double(as[q], ac[q]);
+                    }
+                    split_double(v, vh[r], vl[r]);
+                }
+                named_bar(1, kBNCONS);
+                // ---- O1': h_l = Y(:, l)' v1 (per-thread rows, per-warp float-float sums, warps in order)
+                if (k > 0)
+                    ystream([&](int64_t, float& hi, float& lo) { hi = lo = 0.f; },
+                            [&](const float* yh, const float* yl, const float*, const float*, int64_t l0, int lc) {
+                                for (int l = 0; l < lc; ++l) {
+                                    float s = 0.f, c = 0.f;
+#pragma unroll
+                                    for (int q = 0; q < kBQR; ++q) {
+                                        const int64_t r = tid + (int64_t)kBNCONS * q;
+                                        if (r >= ldp) break;
+                                        ff_mac2(s, c, yh[l * ldp + r], yl[l * ldp + r], vh[r], vl[r]);
+                                    }
+                                    warp_sum_ff(s, c);
+                                    if (lane == 0) {
+                                        wps[warp * kBMaxLC + l] = s;
+                                        wpc[warp * kBMaxLC + l] = c;
+                                    }
+                                }
+                            },
+                            [&](int64_t l0, int lc) {
+                                for (int l = tid; l < lc; l += kBNCONS) {
+                                    float s = wps[l], c = wpc[l];
+                                    for (int w = 1; w < kBNW; ++w) ff_add(s, c, wps[w * kBMaxLC + l], wpc[w * kBMaxLC + l]);
+                                    hacc[l0 + l] = ff_to_double(s, c);
+                                }
+                            });
+                // ---- O3: v2 = v1 - Y h, ||v2||^2
+#pragma unroll
+                for (int q = 0; q < kBQR; ++q) as[q] = ac[q] = 0.f;
+                if (k > 0)
+                    ystream([&](int64_t l, float& hi, float& lo) { split_double(hacc[l], hi, lo); },
+                            [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
+#pragma unroll
+                                for (int q = 0; q < kBQR; ++q) {
+                                    const int64_t r = tid + (int64_t)kBNCONS * q;
+                                    if (r >= ldp) break;
+                                    for (int l = 0; l < lc; ++l)
+                                        ff_mac2(as[q], ac[q], yh[l * ldp + r], yl[l * ldp + r], ch[l], cl[l]);
+                                }
+                            },
+                            nopost);
+                double nrm = 0.0;
+#pragma unroll
+                for (int q = 0; q < kBQR; ++q) {
+                    const int64_t r = tid + (int64_t)kBNCONS * q;
+                    if (r >= ldp) break;
+                    double v = 0.0;
+                    if (r < m) v = ((double)vh[r] + (double)vl[r]) - ff_to_double(as[q], ac[q]);
+                    split_double(v, vh[r], vl[r]);  // v2 replaces v1 (each thread owns its rows)
+                    nrm += v * v;
+                }
+                nrm = warp_sum_double(nrm);
+                if (lane == 0) red[warp] = nrm;
+            }
+            ok = __syncthreads_and(ok) != 0;
+            if (!ok) break;
+            // ---- nu, certified E_cur of basis k-1, stop tests of steps 2.2 / 2.4
+            if (tid == 0) {
+                double acc = 0.0;
+                for (int w = 0; w < kBNW; ++w) acc += red[w];
+                const double nuv = sqrt(acc);
+                const double xin = sqrt(__ldcg(&I.xn2[piv]));
+                int32_t st = STOP_NONE;
+                if (k > 0) {
+                    if (I.mode == MODE_FRO_REL) {
+                        if (fro_prev <= fro_tol) st = STOP_TOL;
+                    } else if (nuv <= eps_r) {
+                        st = STOP_TOL;
+                    }
+                }
+                if (st == STOP_NONE && k >= dmax) st = STOP_DMAX;
+                if (st == STOP_NONE && (nuv < eps_r22 || nuv <= kRankFloor * xin)) st = STOP_BREAK;
+                if (k > 0) I.err[k - 1] = nuv;
+                if (st == STOP_NONE) {
+                    I.piv[k] = piv;
+                    if (I.nu) I.nu[k] = nuv;
+                }
+                bc[2] = nuv;
+                flag[1] = st;
+            }
+            __syncthreads();
+            const double nuv = bc[2];
+            if (k > 0) err_last = nuv;
+            stop = flag[1];
+            if (stop != STOP_NONE) break;
+
+            // ---- xi = v2 / nu: Y(:, k), its split copy, and the pass vector in shared memory
+            const double inv_nu = 1.0 / nuv;
+            if (warp < kBNW) {
+#pragma unroll
+                for (int q = 0; q < kBQR; ++q) {
+                    const int64_t r = tid + (int64_t)kBNCONS * q;
+                    if (r >= ldp) break;
+                    const double y = ((double)vh[r] + (double)vl[r]) * inv_nu;
+                    if (r < m) I.Y[r + k * I.ldy] = y;
+                    split_double(y, vh[r], vl[r]);
+                    I.ys[k * ldp + r] = vh[r];
+                    I.ys[(dmax + k) * ldp + r] = vl[r];
+                }
+                fence_proxy_async_global();  // Y's split copy is read by bulk copies later
+            }
+            __syncthreads();
+
+            // ---- the fused pass
+            if (warp == kBNW) {
+                if (lane == 0 && ok) {
+                    int64_t g = 0, t = 0;
+                    for (int64_t u = 0; u < W; ++u) {
+                        if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t rows = (uint32_t)min((int64_t)kBMT, ldp - t * kBMT);
+                        const uint32_t bytes = (uint32_t)(kBC * P) * rows * 4u;
+                        mbar_arrive_expect_tx(&full[ps], bytes);
+                        bulk_g2s(ring + (size_t)ps * STAGE_F, I.planes + g * kBC * P * ldp + t * kBC * P * kBMT, bytes,
+                                 &full[ps], pol_x);
+                        if (++ps == S) {
+                            ps = 0;
+                            pph ^= 1u;
+                            preuse = true;
+                        }
+                        if (++t == NT) {
+                            t = 0;
+                            ++g;
+                        }
+                    }
+                }
+            } else {
+                float acc_s[kBCPW][4], acc_c[kBCPW][4];
+#pragma unroll
+                for (int qq = 0; qq < kBCPW; ++qq)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
+                double best_e = -1.0, esum = 0.0;
+                int64_t best_j = INT64_MAX;
+                double e_old[kBCPW] = {0.0, 0.0};
+                int64_t g = 0, t = 0;
+                for (int64_t u = 0; u < W; ++u) {
+                    const int s = cs;
+                    const uint32_t ph = cph;
+                    if (++cs == S) {
+                        cs = 0;
+                        cph ^= 1u;
+                    }
+                    const int64_t c0 = g * kBC;
+                    const int ncols = (int)min((int64_t)kBC, n - c0);
+                    if (t == 0 && lane == 0) {
+#pragma unroll
+                        for (int qq = 0; qq < kBCPW; ++qq) {
+                            const int cw = warp * kBCPW + qq;
+                            e_old[qq] = (cw < ncols) ? __ldcg(&I.e[c0 + cw]) : 0.0;
+                        }
+                    }
+                    if (ok && !mbar_wait(&full[s], ph)) ok = false;
+                    const int rows = (int)min((int64_t)kBMT, ldp - t * kBMT);
+                    if (ok) {
+                        const float* st = ring + (size_t)s * STAGE_F;
+                        if (rows == kBMT)
+                            consume_tile_xi<P, kBCPW, kBMT, true>(st, vh + t * kBMT, vl + t * kBMT, kBMT, warp, lane,
+                                                                  acc_s, acc_c);
+                        else
+                            consume_tile_xi<P, kBCPW, kBMT, false>(st, vh + t * kBMT, vl + t * kBMT, rows, warp, lane,
+                                                                   acc_s, acc_c);
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                    if (++t < NT) continue;
+                    t = 0;
+                    // end of column group g: T(k, j), e_j, the running argmax
+#pragma unroll
+                    for (int qq = 0; qq < kBCPW; ++qq) {
+                        float sq = acc_s[qq][0], cq = acc_c[qq][0];
+#pragma unroll
+                        for (int e = 1; e < 4; ++e) ff_add(sq, cq, acc_s[qq][e], acc_c[qq][e]);
+                        warp_sum_ff(sq, cq);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
+                        const int cw = warp * kBCPW + qq;
+                        if (lane == 0 && cw < ncols) {
+                            const int64_t j = c0 + cw;
+                            const double cj = ff_to_double(sq, cq);
+                            I.T[j * I.ldt + k] = cj;
+                            const double en = (j == piv) ? 0.0 : fmax(e_old[qq] - cj * cj, 0.0);
+                            I.e[j] = en;
+                            esum += en;
+                            if (better(en, j, best_e, best_j)) {
+                                best_e = en;
+                                best_j = j;
+                            }
+                        }
+                    }
+                    ++g;
+                }
+                if (lane == 0) {
+                    red[warp] = best_e;
+                    redj[warp] = best_j;
+                    red[kBNW + warp] = esum;
+                }
+            }
+            ok = __syncthreads_and(ok) != 0;
+            if (!ok) break;
+            // ---- argmax over the warps, Frobenius residual (fixed order)
+            if (tid == 0) {
+                double be = -1.0, fs = 0.0;
+                int64_t bj = INT64_MAX;
+                for (int w = 0; w < kBNW; ++w) {
+                    if (better(red[w], redj[w], be, bj)) {
+                        be = red[w];
+                        bj = redj[w];
+                    }
+                    fs += red[kBNW + w];
+                }
+                bc[3] = sqrt(fmax(fs, 0.0));
+                redj[kBNW] = (bj >= 0 && bj < n) ? bj : piv;
+            }
+            __syncthreads();
+            fro_prev = bc[3];
+            piv = redj[kBNW];
+            ++k;
+            __syncthreads();
+        }
+        // ---- result of this matrix
+        if (tid == 0) {
+            rbd_batch_result rr;
+            rr.d = k;
+            rr.next_pivot = piv;
+            rr.stop_reason = ok ? stop : STOP_BREAK;
+            rr.status = ok ? st0 : ST_ETIMEOUT;
+            rr.err_last = (k > 0) ? err_last : 0.0;
+            rr.fro_last = fro_prev;
+            rr.x_fro = x_fro;
+            rr.x_maxcol = x_maxcol;
+            bp.res[idx] = rr;
+        }
+        __syncthreads();
+        if (!ok) break;
+    }
+}
+
+template <int P>
+size_t batch_smem() {
+    return (size_t)kBRingBytes + (size_t)(2 * BCfg<P>::SMAX + 2) * 8 + (size_t)2 * kBMaxRows * 4 + (size_t)kBMaxD * 8 +
+           (size_t)4 * kBMaxLC * 4 + (size_t)2 * kBNW * kBMaxLC * 4 + (size_t)(4 * kBNW + 16) * 8;
+}
+
+}  // namespace
+}  // namespace rbd
+
+// ==================================================================== host: plans
+struct rbd_batch_plan_s {
+    int xt = 0;
+    int64_t count = 0;
+    int S = 0;
+    int num_sms = 0;
+    size_t smem = 0;
+    int init_blocks = 0;
+    rbd::BInst* d_inst = nullptr;
+    int32_t* d_order = nullptr;
+    int64_t* d_colstart = nullptr;
+    uint32_t* d_queue = nullptr;  // followed by the status array (count int32)
+    int32_t* d_status = nullptr;
+    size_t zero_bytes = 0;
+};
+
+using namespace rbd;
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t inst, order, colstart, queue, status, per_begin, total;
+    std::vector<size_t> planes, ys, e, xn2;
+};
+
+rbd_status check_inst(const rbd_instance& I, rbd_dtype xt) {
+    if (!I.X || !I.Y || !I.T || !I.pivots || !I.err) return RBD_EINVAL;
+    if (I.m < 1 || I.n < 1 || I.ldx < I.m || I.ldy < I.m || I.d_max < 1 || I.ldt < I.d_max) return RBD_EINVAL;
+    if (I.d_max > I.m || I.d_max > I.n) return RBD_EINVAL;
+    if (I.start < 0 || I.start >= I.n) return RBD_EINVAL;
+    if (!(I.tol >= 0.0) || I.tol == __builtin_inf()) return RBD_EINVAL;
+    if (I.mode != RBD_TOL_MAXCOL_ABS && I.mode != RBD_TOL_MAXCOL_REL && I.mode != RBD_TOL_FRO_REL) return RBD_EINVAL;
+    if (xt != RBD_F64 && xt != RBD_F32) return RBD_EUNSUPPORTED;
+    if (round_up(I.m, 128) > kBMaxRows || I.d_max > kBMaxD) return RBD_EUNSUPPORTED;
+    if (I.n > ((int64_t)1 << 31)) return RBD_EUNSUPPORTED;
+    return RBD_OK;
+}
+
+bool make_layout(const rbd_instance* inst, int64_t count, rbd_dtype xt, Layout& L) {
+    const int P = (xt == RBD_F64) ? 2 : 1;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off = al256(off + b);
+        return o;
+    };
+    L.queue = take(4);
+    L.status = take((size_t)count * 4);
+    L.per_begin = off;
+    L.inst = take((size_t)count * sizeof(BInst));
+    L.order = take((size_t)count * 4);
+    L.colstart = take((size_t)(count + 1) * 8);
+    L.planes.resize(count);
+    L.ys.resize(count);
+    L.e.resize(count);
+    L.xn2.resize(count);
+    for (int64_t i = 0; i < count; ++i) {
+        if (check_inst(inst[i], xt) != RBD_OK) return false;
+        const int64_t ldp = round_up(inst[i].m, 128);
+        const int64_t ng = ceil_div(inst[i].n, (int64_t)kBC);
+        L.planes[i] = take((size_t)ng * kBC * P * ldp * 4);
+        L.ys[i] = take((size_t)2 * inst[i].d_max * ldp * 4);
+        L.e[i] = take((size_t)inst[i].n * 8);
+        L.xn2[i] = take((size_t)inst[i].n * 8);
+    }
+    L.total = off;
+    return true;
+}
+
+rbd_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return RBD_OK;
+    if (e == cudaErrorMemoryAllocation) return RBD_ENOMEM;
+    return RBD_ECUDA;
+}
+
+std::mutex g_battr_mu;
+bool g_battr_done[64] = {};
+
+cudaError_t batch_setup(int dev) {
+    std::lock_guard<std::mutex> lk(g_battr_mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (g_battr_done[dev]) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem<1>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem<2>());
+    if (e == cudaSuccess) g_battr_done[dev] = true;
+    return e;
+}
+
+rbd_status run_with(rbd_batch_plan p, rbd_batch_result* results, cudaStream_t st, int S) {
+    BatchParams bp;
+    bp.inst = p->d_inst;
+    bp.count = p->count;
+    bp.order = p->d_order;
+    bp.colstart = p->d_colstart;
+    bp.queue = p->d_queue;
+    bp.status = p->d_status;
+    bp.res = results;
+    bp.S = S;
+    cudaError_t e = cudaMemsetAsync(p->d_queue, 0, p->zero_bytes, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (p->xt == RBD_F64) {
+        batch_init_kernel<2><<<p->init_blocks, 256, 0, st>>>(bp);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            batch_kernel<2><<<p->num_sms, kBThreads, p->smem, st>>>(bp);
+            e = cudaGetLastError();
+        }
+    } else {
+        batch_init_kernel<1><<<p->init_blocks, 256, 0, st>>>(bp);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            batch_kernel<1><<<p->num_sms, kBThreads, p->smem, st>>>(bp);
+            e = cudaGetLastError();
+        }
+    }
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rbd_batch_workspace_bytes(const rbd_instance* inst, int64_t count, rbd_dtype xt) {
+    if (!inst || count < 1) return 0;
+    Layout L;
+    if (!make_layout(inst, count, xt, L)) return 0;
+    return L.total;
+}
+
+rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst, int64_t count, rbd_dtype xt,
+                                 void* workspace, size_t workspace_bytes, void* stream) {
+    if (!plan || !inst || count < 1 || count > ((int64_t)1 << 30)) return RBD_EINVAL;
+    *plan = nullptr;
+    for (int64_t i = 0; i < count; ++i) {
+        const rbd_status s = check_inst(inst[i], xt);
+        if (s != RBD_OK) return s;
+    }
+    Layout L;
+    if (!make_layout(inst, count, xt, L)) return RBD_EINVAL;
+    if (!workspace || ((uintptr_t)workspace & 255u) != 0) return RBD_EINVAL;
+    if (workspace_bytes < L.total) return RBD_ENOMEM;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    int sms = 0;
+    ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce == cudaSuccess) ce = batch_setup(dev);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(ce);
+    }
+    const int P = (xt == RBD_F64) ? 2 : 1;
+    unsigned char* base = (unsigned char*)workspace;
+    std::vector<BInst> hi(count);
+    std::vector<int64_t> colstart(count + 1, 0);
+    std::vector<double> cost(count);
+    for (int64_t i = 0; i < count; ++i) {
+        const rbd_instance& s = inst[i];
+        BInst& b = hi[i];
+        std::memset(&b, 0, sizeof(b));
+        b.X = s.X;
+        b.m = s.m;
+        b.n = s.n;
+        b.ldx = s.ldx;
+        b.ldp = round_up(s.m, 128);
+        b.ngroups = ceil_div(s.n, (int64_t)kBC);
+        b.NT = ceil_div(b.ldp, (int64_t)kBMT);
+        b.tol = s.tol;
+        b.mode = s.mode;
+        b.d_max = s.d_max;
+        b.start = s.start;
+        b.Y = s.Y;
+        b.ldy = s.ldy;
+        b.T = s.T;
+        b.ldt = s.ldt;
+        b.piv = s.pivots;
+        b.err = s.err;
+        b.nu = s.nu;
+        b.planes = (float*)(base + L.planes[i]);
+        b.ys = (float*)(base + L.ys[i]);
+        b.e = (double*)(base + L.e[i]);
+        b.xn2 = (double*)(base + L.xn2[i]);
+        colstart[i + 1] = colstart[i] + b.ngroups * kBC;
+        cost[i] = (double)b.ldp * (double)b.n * (double)P * (double)std::min<int64_t>(s.d_max, 64) +
+                  (double)b.ldp * (double)s.d_max * (double)s.d_max;
+    }
+    std::vector<int32_t> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    cudaStream_t st = (cudaStream_t)stream;
+    ce = cudaMemcpyAsync(base + L.inst, hi.data(), (size_t)count * sizeof(BInst), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(base + L.order, order.data(), (size_t)count * 4, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(base + L.colstart, colstart.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // the host vectors go out of scope
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(ce);
+    }
+    rbd_batch_plan p = new (std::nothrow) rbd_batch_plan_s();
+    if (!p) return RBD_ENOMEM;
+    p->xt = (int)xt;
+    p->count = count;
+    p->S = (P == 2) ? BCfg<2>::SMAX : BCfg<1>::SMAX;
+    p->num_sms = sms;
+    p->smem = (P == 2) ? batch_smem<2>() : batch_smem<1>();
+    p->init_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(colstart[count], 8), (int64_t)sms * 8));
+    p->d_inst = (BInst*)(base + L.inst);
+    p->d_order = (int32_t*)(base + L.order);
+    p->d_colstart = (int64_t*)(base + L.colstart);
+    p->d_queue = (uint32_t*)(base + L.queue);
+    p->d_status = (int32_t*)(base + L.status);
+    p->zero_bytes = L.per_begin;
+    *plan = p;
+    return RBD_OK;
+}
+
+rbd_status rbd_batch_run(rbd_batch_plan plan, rbd_batch_result* results, void* stream) {
+    if (!plan || !results) return RBD_EINVAL;
+    return run_with(plan, results, (cudaStream_t)stream, plan->S);
+}
+
+rbd_status rbd_batch_tune(rbd_batch_plan plan, rbd_batch_result* results, void* stream, int32_t* stages_out) {
+    if (!plan || !results) return RBD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int smax = (plan->xt == RBD_F64) ? BCfg<2>::SMAX : BCfg<1>::SMAX;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return RBD_ECUDA;
+    }
+    rbd_status rs = run_with(plan, results, st, plan->S);  // warm-up
+    float best = 1e30f;
+    int best_s = plan->S;
+    for (int s = 2; s <= smax && rs == RBD_OK; s += (smax >= 6 ? 2 : 1)) {
+        cudaEventRecord(e0, st);
+        rs = run_with(plan, results, st, s);
+        cudaEventRecord(e1, st);
+        if (rs != RBD_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rs = RBD_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_s = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs == RBD_OK) {
+        plan->S = best_s;
+        if (stages_out) *stages_out = best_s;
+    }
+    cudaGetLastError();
+    return rs;
+}
+
+rbd_status rbd_batch_plan_destroy(rbd_batch_plan plan) {
+    delete plan;
+    return RBD_OK;
+}
+
+rbd_status rbd_compress_batched(const rbd_instance* inst, int64_t count, rbd_dtype xt, rbd_batch_result* results,
+                                void* stream) {
+    if (!inst || !results || count < 1) return RBD_EINVAL;
+    const size_t ws_bytes = rbd_batch_workspace_bytes(inst, count, xt);
+    if (ws_bytes == 0) {
+        for (int64_t i = 0; i < count; ++i) {
+            const rbd_status s = check_inst(inst[i], xt);
+            if (s != RBD_OK) return s;
+        }
+        return RBD_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    void* ws = nullptr;
+    void* dres = nullptr;
+    cudaError_t ce = cudaMallocAsync(&ws, ws_bytes, st);
+    if (ce == cudaSuccess) ce = cudaMallocAsync(&dres, (size_t)count * sizeof(rbd_batch_result), st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        if (ws) cudaFreeAsync(ws, st);
+        return RBD_ENOMEM;
+    }
+    rbd_batch_plan plan = nullptr;
+    rbd_status rs = rbd_batch_plan_create(&plan, inst, count, xt, ws, ws_bytes, stream);
+    if (rs == RBD_OK) rs = rbd_batch_run(plan, (rbd_batch_result*)dres, stream);
+    if (rs == RBD_OK) {
+        ce = cudaMemcpyAsync(results, dres, (size_t)count * sizeof(rbd_batch_result), cudaMemcpyDeviceToHost, st);
+        if (ce != cudaSuccess) rs = cuda_status(ce);
+    }
+    cudaFreeAsync(dres, st);
+    cudaFreeAsync(ws, st);
+    ce = cudaStreamSynchronize(st);
+    if (rs == RBD_OK && ce != cudaSuccess) rs = cuda_status(ce);
+    if (plan) rbd_batch_plan_destroy(plan);
+    cudaGetLastError();
+    return rs;
+}
+
+}  // extern "C"

@@ -52,6 +52,41 @@ __device__ __forceinline__ void consume_tile(const float* __restrict__ st, int r
     }
 }
 
+// Same arithmetic as consume_tile, with the pivot vector's rows of this tile taken from separate
+// (hi, lo) arrays (the batched kernel keeps the whole vector in shared memory) and the stage
+// holding only the X tile: column c plane p at (c*P + p)*rows.
+template <int P, int CPW, int MT, bool FULL>
+__device__ __forceinline__ void consume_tile_xi(const float* __restrict__ st, const float* __restrict__ xh,
+                                                const float* __restrict__ xl, int rows, int warp, int lane,
+                                                float (&acc_s)[CPW][4], float (&acc_c)[CPW][4]) {
+    const int R = FULL ? MT : rows;
+    const int nsl = FULL ? MT / 128 : (rows >> 7);
+#pragma unroll
+    for (int sl = 0; sl < MT / 128; ++sl) {
+        if (!FULL && sl >= nsl) break;
+        const int off = sl * 128 + lane * 4;
+        const float4 zh = *reinterpret_cast<const float4*>(xh + off);
+        const float4 zl = *reinterpret_cast<const float4*>(xl + off);
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+            const float* col = st + (warp * CPW + q) * P * R + off;
+            const float4 a = *reinterpret_cast<const float4*>(col);
+            if (P == 2) {
+                const float4 al = *reinterpret_cast<const float4*>(col + R);
+                ff_mac2(acc_s[q][0], acc_c[q][0], a.x, al.x, zh.x, zl.x);
+                ff_mac2(acc_s[q][1], acc_c[q][1], a.y, al.y, zh.y, zl.y);
+                ff_mac2(acc_s[q][2], acc_c[q][2], a.z, al.z, zh.z, zl.z);
+                ff_mac2(acc_s[q][3], acc_c[q][3], a.w, al.w, zh.w, zl.w);
+            } else {
+                ff_mac1(acc_s[q][0], acc_c[q][0], a.x, zh.x, zl.x);
+                ff_mac1(acc_s[q][1], acc_c[q][1], a.y, zh.y, zl.y);
+                ff_mac1(acc_s[q][2], acc_c[q][2], a.z, zh.z, zl.z);
+                ff_mac1(acc_s[q][3], acc_c[q][3], a.w, zh.w, zl.w);
+            }
+        }
+    }
+}
+
 // BF16 storage (the precision form): FP32 products of the exact BF16 values with the leading
 // FP32 part of the pivot vector, summed in FP32 over the unit's rows (16 per lane) and folded into
 // the float-float accumulator once per unit.  Stage layout as above with BF16 columns.

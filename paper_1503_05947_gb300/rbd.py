@@ -46,6 +46,16 @@ class _Profile(ctypes.Structure):
                 ("loop_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class _Instance(ctypes.Structure):
+    _fields_ = [("X", _PTR), ("m", _I64), ("n", _I64), ("ldx", _I64), ("tol", _DBL), ("mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("d_max", _I64), ("start", _I64), ("Y", _PTR), ("ldy", _I64),
+                ("T", _PTR), ("ldt", _I64), ("pivots", _PTR), ("err", _PTR), ("nu", _PTR)]
+
+
+# rbd_batch_result as a numpy record (device results are copied as bytes)
+_BATCH_RESULT_BYTES = 56  # sizeof(rbd_batch_result)
+
+
 _lib = None
 
 
@@ -78,6 +88,19 @@ def load():
     lib.rbd_grad.restype = ctypes.c_int
     lib.rbd_grad.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _PTR, _I64, _PTR, _I64, _PTR, _I64, _PTR, _I64,
                              _I64, _DBL, _DBL, _PTR, _I64, _PTR, _PTR]
+    lib.rbd_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.rbd_batch_workspace_bytes.argtypes = [ctypes.POINTER(_Instance), _I64, ctypes.c_int]
+    lib.rbd_batch_plan_create.restype = ctypes.c_int
+    lib.rbd_batch_plan_create.argtypes = [ctypes.POINTER(_PTR), ctypes.POINTER(_Instance), _I64, ctypes.c_int, _PTR,
+                                          ctypes.c_size_t, _PTR]
+    lib.rbd_batch_run.restype = ctypes.c_int
+    lib.rbd_batch_run.argtypes = [_PTR, _PTR, _PTR]
+    lib.rbd_batch_tune.restype = ctypes.c_int
+    lib.rbd_batch_tune.argtypes = [_PTR, _PTR, _PTR, ctypes.POINTER(ctypes.c_int32)]
+    lib.rbd_batch_plan_destroy.restype = ctypes.c_int
+    lib.rbd_batch_plan_destroy.argtypes = [_PTR]
+    lib.rbd_compress_batched.restype = ctypes.c_int
+    lib.rbd_compress_batched.argtypes = [ctypes.POINTER(_Instance), _I64, ctypes.c_int, _PTR, _PTR]
     lib.rbd_project.restype = ctypes.c_int
     lib.rbd_project.argtypes = [_PTR, _I64, _I64, _I64, _PTR, ctypes.c_int, _I64, _I64, _PTR, _I64, _PTR]
     lib.rbd_set_profiling.restype = None
@@ -316,3 +339,99 @@ def get_profile() -> dict:
 
 def version() -> int:
     return int(load().rbd_version())
+
+
+class BatchPlan:
+    """The batched form: many column-major CUDA matrices of one dtype (float64 or float32), each
+    with its own tolerance, mode, d_max and start column, compressed in one persistent launch.
+
+    ``items`` is a list of dicts {X, tol, d_max, tol_mode="maxcol_abs", start=0}.  The plan owns the
+    outputs (per matrix Y, T, pivots, err, nu), the workspace and the device result array.
+    ``run()`` only enqueues work on the current stream (capturable in a CUDA graph);
+    ``results()`` synchronises and returns the per-matrix summaries; ``compressed(i)`` the outputs
+    of matrix i trimmed to its d."""
+
+    def __init__(self, items, device=None):
+        lib = load()
+        if not items:
+            raise ValueError("empty batch")
+        X0 = items[0]["X"]
+        self.dtype = X0.dtype
+        if self.dtype not in (torch.float64, torch.float32):
+            raise ValueError("the batched form takes float64 or float32 matrices")
+        self.device = torch.device(device) if device is not None else X0.device
+        self.items = items
+        self.out = []
+        inst = (_Instance * len(items))()
+        for i, it in enumerate(items):
+            X = it["X"]
+            if X.dtype != self.dtype or X.device != self.device:
+                raise ValueError("all matrices must share dtype and device")
+            m, n = X.shape
+            ldx = _colmajor(X, "X")
+            d_max = int(it["d_max"])
+            o = {"Y": colmajor_empty(m, d_max, torch.float64, self.device),
+                 "T": colmajor_empty(d_max, n, torch.float64, self.device),
+                 "pivots": torch.empty(d_max, dtype=torch.int64, device=self.device),
+                 "err": torch.empty(d_max, dtype=torch.float64, device=self.device),
+                 "nu": torch.empty(d_max, dtype=torch.float64, device=self.device)}
+            self.out.append(o)
+            inst[i] = _Instance(X.data_ptr(), m, n, ldx, float(it.get("tol", 0.0)),
+                                TOL_MODES[it.get("tol_mode", "maxcol_abs")], 0, d_max, int(it.get("start", 0)),
+                                o["Y"].data_ptr(), m, o["T"].data_ptr(), d_max, o["pivots"].data_ptr(),
+                                o["err"].data_ptr(), o["nu"].data_ptr())
+        self._inst = inst
+        count = len(items)
+        nbytes = int(lib.rbd_batch_workspace_bytes(inst, count, DTYPES[self.dtype]))
+        if nbytes == 0:
+            # an invalid or unsupported descriptor: plan creation reports which
+            plan = _PTR()
+            _check(lib.rbd_batch_plan_create(ctypes.byref(plan), inst, count, DTYPES[self.dtype], None, 0,
+                                             _stream_ptr(self.device)), "rbd_batch_plan_create")
+            raise RbdError(1, "rbd_batch_workspace_bytes")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws_ptr = self.workspace.data_ptr() + off
+        self._ws_bytes = nbytes
+        self.res = torch.zeros(count * _BATCH_RESULT_BYTES, dtype=torch.uint8, device=self.device)
+        plan = _PTR()
+        with torch.cuda.device(self.device):
+            st = lib.rbd_batch_plan_create(ctypes.byref(plan), inst, count, DTYPES[self.dtype], self._ws_ptr,
+                                           self._ws_bytes, _stream_ptr(self.device))
+        _check(st, "rbd_batch_plan_create")
+        self._plan = plan
+
+    def run(self):
+        with torch.cuda.device(self.device):
+            _check(load().rbd_batch_run(self._plan, self.res.data_ptr(), _stream_ptr(self.device)), "rbd_batch_run")
+
+    def tune(self) -> int:
+        stages = ctypes.c_int32(0)
+        with torch.cuda.device(self.device):
+            _check(load().rbd_batch_tune(self._plan, self.res.data_ptr(), _stream_ptr(self.device),
+                                         ctypes.byref(stages)), "rbd_batch_tune")
+        return int(stages.value)
+
+    def results(self) -> list:
+        import numpy as np
+        raw = self.res.cpu().numpy()
+        rec = np.dtype([("d", "<i8"), ("next_pivot", "<i8"), ("stop_reason", "<i4"), ("status", "<i4"),
+                        ("err_last", "<f8"), ("fro_last", "<f8"), ("x_fro", "<f8"), ("x_maxcol", "<f8")])
+        arr = raw.view(rec)
+        return [{k: arr[i][k].item() for k in rec.names} for i in range(len(self.items))]
+
+    def compressed(self, i: int, res: Optional[dict] = None) -> Compressed:
+        r = res if res is not None else self.results()[i]
+        o = self.out[i]
+        d = int(r["d"])
+        return Compressed(o["Y"][:, :d], o["T"][:d, :], o["pivots"][:d], o["err"][:d], o["nu"][:d], d,
+                          int(r["next_pivot"]), STOP_REASONS.get(int(r["stop_reason"]), "?"), float(r["err_last"]),
+                          float(r["fro_last"]), float(r["x_fro"]), float(r["x_maxcol"]), 2)
+
+    def __del__(self):
+        try:
+            if getattr(self, "_plan", None):
+                load().rbd_batch_plan_destroy(self._plan)
+                self._plan = None
+        except Exception:
+            pass
