@@ -313,6 +313,7 @@ def run_gpu(args, world, rank, local):
     forms = {}
     if rank == 0 and not args.no_forms:
         forms["precision"] = precision_forms(dev)
+        forms["batched"] = batched_forms(dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -399,6 +400,109 @@ def precision_forms(dev) -> dict:
     return out
 
 
+BATCH_WORKLOAD = ("2048 FP32 matrices U diag(s) V' (Haar U, V; s_i = exp(-r i), r ~ U[0.05, 0.5], truncated at 1e-9), "
+                  "m log-uniform in [256, 4096], n log-uniform in [64, 2048], tol log-uniform in [1e-6, 1e-2] "
+                  "(relative max-column), d_max = min(m, n, 512) (seed 3)")
+
+
+def batched_forms(dev) -> dict:
+    """The batched form: the 2048-matrix workload compressed by one persistent launch captured in a
+    CUDA graph (pipeline depth chosen by the plan's autotuner), against the single-matrix path
+    (rbd_compress per matrix, FP32 and FP64 copies) timed on a seeded sample of 64 matrices and
+    scaled to the whole batch by sum((d + 1) m n)."""
+    import torch
+
+    import gen
+    import paper_1503_05947_gb300 as rbd
+    specs = gen.batch_specs(2048, seed=3)
+    items = []
+    for sp in specs:
+        s = gen.decay_spectrum(sp["rate"], min(sp["m"], sp["n"]))
+        X = gen.lowrank_torch(sp["m"], sp["n"], s, sp["seed"], device=dev, dtype=torch.float32)
+        items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"]})
+    plan = rbd.BatchPlan(items)
+    stages = plan.tune()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        plan.run()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.run()
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    res = plan.results()
+    cost = [(r["d"] + 1) * it["X"].shape[0] * it["X"].shape[1] for r, it in zip(res, items)]
+    xbytes = 4.0 * sum(cost)
+    rng = np.random.default_rng(7)
+    sample = sorted(rng.choice(len(items), 64, replace=False).tolist())
+    scale = sum(cost) / sum(cost[i] for i in sample)
+
+    def single(dtype):
+        Xs = [items[i]["X"] if dtype == torch.float32 else items[i]["X"].t().contiguous().double().t() for i in sample]
+        for i, X in zip(sample[:2], Xs[:2]):
+            rbd.compress(X, items[i]["tol"], items[i]["d_max"], tol_mode="maxcol_rel")
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i, X in zip(sample, Xs):
+            rbd.compress(X, items[i]["tol"], items[i]["d_max"], tol_mode="maxcol_rel")
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) * 1e3 * scale
+
+    s32 = single(torch.float32)
+    s64 = single(torch.float64)
+    out = {"workload": BATCH_WORKLOAD, "matrices": len(items), "stages": stages, "graph": True, "ms": ms,
+           "bases_total": int(sum(r["d"] for r in res)), "x_bytes_streamed": xbytes, "gbs": xbytes / (ms * 1e-3) / 1e9,
+           "single_matrix_f32_ms_est": s32, "speedup_vs_single_f32": s32 / ms,
+           "single_matrix_f64_ms_est": s64, "speedup_vs_single_f64": s64 / ms,
+           "single_sample": "64 seeded matrices compressed one by one (rbd_compress, synchronous calls), "
+                            "scaled by sum((d + 1) m n)"}
+    del plan, items, graph
+    torch.cuda.empty_cache()
+    return out
+
+
+def profile_case(name: str):
+    """Short, fixed launches of one kernel for profiler captures (not a bench line):
+    bf16-small: the persistent kernel on the parametric snapshots 16384 x 4096 stored in BF16;
+    batched-small: the batched form on the first 256 matrices of the 2048-matrix workload."""
+    import torch
+
+    import gen
+    import paper_1503_05947_gb300 as rbd
+    dev = torch.device("cuda", 0)
+    if name == "bf16-small":
+        X = gen.parametric_snapshots_torch(16384, 4096, device=dev).t().contiguous().to(torch.bfloat16).t()
+        for _ in range(2):
+            r = rbd.compress(X, 0.0, 32)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"case": name, "bases": r.d}))
+    elif name == "batched-small":
+        items = []
+        for sp in gen.batch_specs(2048, seed=3)[:256]:
+            s = gen.decay_spectrum(sp["rate"], min(sp["m"], sp["n"]))
+            X = gen.lowrank_torch(sp["m"], sp["n"], s, sp["seed"], device=dev, dtype=torch.float32)
+            items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"]})
+        plan = rbd.BatchPlan(items)
+        for _ in range(2):
+            plan.run()
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"case": name, "bases": int(sum(r["d"] for r in plan.results()))}))
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+
+
 def gen_x64(q):
     import gen
     return gen.u8_to_unit_f64(q)
@@ -417,7 +521,12 @@ def main():
                     help="basis limit; values below 512 give the short profiling case, not a bench line")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (end-to-end) measurement")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / batched form measurements")
+    ap.add_argument("--profile-case", choices=["bf16-small", "batched-small"], default=None,
+                    help="run one short fixed case for a profiler capture instead of the bench")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     world, rank, local = dist_setup()
     global D_MAX
     D_MAX = args.d_max
