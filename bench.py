@@ -419,7 +419,8 @@ def batched_forms(dev) -> dict:
     for sp in specs:
         s = gen.decay_spectrum(sp["rate"], min(sp["m"], sp["n"]))
         X = gen.lowrank_torch(sp["m"], sp["n"], s, sp["seed"], device=dev, dtype=torch.float32)
-        items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"]})
+        items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"],
+                          "d_hint": sp["d_hint"]})
     plan = rbd.BatchPlan(items)
     stages = plan.tune()
     side = torch.cuda.Stream(dev)
@@ -493,7 +494,8 @@ def profile_case(name: str):
         for sp in gen.batch_specs(2048, seed=3)[:256]:
             s = gen.decay_spectrum(sp["rate"], min(sp["m"], sp["n"]))
             X = gen.lowrank_torch(sp["m"], sp["n"], s, sp["seed"], device=dev, dtype=torch.float32)
-            items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"]})
+            items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"],
+                          "d_hint": sp["d_hint"]})
         plan = rbd.BatchPlan(items)
         for _ in range(2):
             plan.run()

@@ -214,8 +214,11 @@ def batch_specs(count: int = 2048, seed: int = 3):
     n = np.rint(np.exp(rng.uniform(np.log(64), np.log(2048), count))).astype(np.int64)
     r = rng.uniform(0.05, 0.5, count)
     tol = np.exp(rng.uniform(np.log(1e-6), np.log(1e-2), count))
+    # expected number of bases: the tolerance is reached where exp(-r d) ~ tol (a scheduling hint)
     return [{"m": int(m[i]), "n": int(n[i]), "rate": float(r[i]), "tol": float(tol[i]),
-             "d_max": int(min(m[i], n[i], 512)), "seed": seed * 100003 + i} for i in range(count)]
+             "d_max": int(min(m[i], n[i], 512)), "seed": seed * 100003 + i,
+             "d_hint": int(min(min(m[i], n[i], 512), np.ceil(np.log(1.0 / tol[i]) / r[i]) + 1))}
+            for i in range(count)]
 
 
 def decay_spectrum(rate: float, r_max: int) -> np.ndarray:

@@ -200,8 +200,10 @@ rbd_status rbd_project(const double* Y, int64_t m, int64_t d, int64_t ldy,
 /*
  * Batched form (an extension: the paper compresses one matrix at a time): many independent
  * matrices, each with its own sizes, tolerance and outputs, compressed by Algorithm 1 in ONE
- * persistent launch.  Each CTA takes whole matrices from a queue ordered by decreasing size and
- * runs their greedy loops to the end; results match rbd_compress on each matrix.
+ * persistent launch.  The plan orders the matrices by estimated work (m n d, with d the hint or
+ * d_max) and gives the largest a team of up to 16 CTAs; each CTA takes the next member slot from
+ * the queue and runs that matrix's greedy loop with its team to the end.  Results match
+ * rbd_compress on each matrix and do not depend on the team sizes.
  *
  * Limits: every matrix has m <= 4096 rows and d_max <= 512 (larger matrices: rbd_compress);
  * storage type RBD_F64 or RBD_F32, the same for the whole batch.
@@ -211,7 +213,9 @@ typedef struct rbd_instance {
     int64_t m, n, ldx;
     double tol;           /* epsilon_R, interpreted by `mode` (an rbd_tol_mode) */
     int32_t mode;
-    int32_t reserved;
+    int32_t d_hint;       /* expected number of bases, or 0 (= d_max): used only to order the
+                             queue and size teams of CTAs for large matrices; results do not
+                             depend on it */
     int64_t d_max;        /* 1 <= d_max <= min(m, n, 512) */
     int64_t start;        /* 0 <= start < n */
     double* Y;            /* device outputs as for rbd_compress */

@@ -1,21 +1,27 @@
 // rbd_batch.cu -- the batched form: many independent matrices, each compressed by Algorithm 1,
-// in one persistent launch.
+// in one persistent cooperative launch.
 //
 // batch_init_kernel  the initial pass over every matrix (Section 3.3's pre-computation with
 //                    A = I): e_j = ||x_j||^2 and the tile-major re-layout of X, one warp per
 //                    column of the whole batch.
-// batch_kernel       one CTA per SM; each CTA takes the next matrix from a queue ordered by
-//                    decreasing size (largest first keeps the tail short) and runs its whole
-//                    greedy loop alone, so no grid-wide synchronisation is needed:
+// batch_kernel       one CTA per SM.  The plan gives each matrix a TEAM of t CTAs (t = 1 for most;
+//                    large matrices get up to 16 so that no single matrix outlasts the batch) and
+//                    lays the matrices' member slots out in a queue ordered by decreasing size; a
+//                    CTA claims the next slot and works as that member until the matrix stops:
 //                      step 2.1-2.2  v1 = x_i - Y t (t = T(0:k, i)), h = Y' v1, v2 = v1 - Y h
-//                                    (classical Gram-Schmidt twice, float-float), nu = ||v2||,
-//                                    stop tests; xi = v2 / nu -> Y(:, k) and shared memory
-//                      fused pass    T(k, :) = xi' X, e_j <- e_j - T(k, j)^2 (Eq. (evalerr),
-//                                    A = I), argmax
-//                    Y (split FP32 planes, column-major, one copy per matrix) and the X tiles
-//                    stream through one ring of shared-memory stages with bulk (TMA) copies;
-//                    xi stays in shared memory for the whole pass.
-// The arithmetic is the persistent loop kernel's (rbd_loop.cu) with G = 1 CTA per matrix.
+//                                    (classical Gram-Schmidt twice, float-float) on the member's
+//                                    block of rows; partial sums of h and ||v2||^2 and the rows of
+//                                    v2 are exchanged through the matrix's team buffers; nu, stop
+//                                    tests (identical in every member); xi = v2 / nu
+//                      fused pass    the member's column groups: T(k, j) = xi' x_j,
+//                                    e_j <- e_j - T(k, j)^2 (Eq. (evalerr), A = I), argmax, then
+//                                    the team's argmax and Frobenius residual
+//                    Three team barriers per basis (none when t = 1).  The members' row blocks of Y
+//                    (split FP32 planes) and the X tiles stream through one ring of shared-memory
+//                    stages with bulk (TMA) copies; xi stays in shared memory for the whole pass.
+// The launch is cooperative (all CTAs resident), and slots are claimed in order, so a member only
+// ever waits for members of its own team whose slots come before any later-claimed work: every team
+// ahead of it is complete and finishes, freeing the CTAs that claim the remaining slots.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -55,7 +61,7 @@ struct BInst {
     const void* X;
     int64_t m, n, ldx, ldp, ngroups, NT;
     double tol;
-    int32_t mode, pad;
+    int32_t mode, team;   // team: CTAs working on this matrix
     int64_t d_max, start;
     double* Y;
     int64_t ldy;
@@ -65,21 +71,40 @@ struct BInst {
     double* err;
     double* nu;
     float* planes;   // tile-major, as in rbd_work.h
-    float* ys;       // split Y: [2][d_max][ldp]
+    float* ys;       // split Y, one block of rb rows per member: [team][2][d_max][rb]
+    int64_t rb;      // rows per member block (team * rb >= ldp)
     double* e;
     double* xn2;
+    // team exchange (team > 1)
+    uint32_t* bar;   // team barrier arrivals (zero before the run)
+    double* hpart;   // [team][d_max]
+    double* nrm;     // [team]
+    float* vbuf;     // [2][ldp] rows of v2 (hi | lo)
+    double* cand_e;  // [team]
+    int64_t* cand_j; // [team]
+    double* frop;    // [team]
 };
 
 struct BatchParams {
     const BInst* inst;
     int64_t count;
-    const int32_t* order;     // claim slot -> matrix
-    const int64_t* colstart;  // padded-column prefix sums (count + 1)
-    uint32_t* queue;          // claim counter (zero before the run)
-    int32_t* status;          // per matrix (zero before the run)
+    int64_t nslots;
+    const int32_t* slot_inst;    // claim slot -> matrix
+    const int32_t* slot_member;  // claim slot -> member index in the matrix's team
+    const int64_t* colstart;     // padded-column prefix sums (count + 1)
+    uint32_t* queue;             // claim counter (zero before the run)
+    int32_t* status;             // per matrix (zero before the run)
     rbd_batch_result* res;
-    int S;                    // ring stages used by the pass (<= SMAX)
+    int S;                       // ring stages used by the pass (<= SMAX)
 };
+
+constexpr uint64_t kTeamWaitNs = 10000000000ull;  // a member may wait for teams ahead to finish
+
+__device__ __forceinline__ uint32_t ld_acquire_u32b(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // ---------------------------------------------------------------- initial pass
 template <int P>
@@ -192,13 +217,42 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
         __syncthreads();
         const int64_t slot = flag[0];
         __syncthreads();
-        if (slot >= bp.count) break;
-        const int64_t idx = bp.order[slot];
+        if (slot >= bp.nslots) break;
+        const int64_t idx = bp.slot_inst[slot];
+        const int mb = bp.slot_member[slot];
         const BInst I = bp.inst[idx];
-        const int64_t m = I.m, n = I.n, ldp = I.ldp, dmax = I.d_max, NT = I.NT;
-        const int64_t W = I.ngroups * NT;
+        const int tm = I.team;
+        const int64_t m = I.m, n = I.n, ldp = I.ldp, dmax = I.d_max, NT = I.NT, rb = I.rb;
+        const int64_t r_lo = (int64_t)mb * rb, r_hi = min(ldp, r_lo + rb);  // this member's rows
+        const int64_t g_lo = (I.ngroups * mb) / tm, g_hi = (I.ngroups * (mb + 1)) / tm;  // its groups
+        const int64_t W = (g_hi - g_lo) * NT;
+        const float* ysb = I.ys + (int64_t)mb * 2 * dmax * rb;  // this member's block of Y
+        uint32_t tepoch = 0;
 
-        // ---- statistics of the initial pass and the tolerances (fixed order)
+        // team barrier: every thread of every member; false if the wait ran out
+        auto team_sync = [&]() {
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                const uint32_t target = (uint32_t)tm * (++tepoch);
+                atomicAdd(I.bar, 1u);
+                int good = 1;
+                if (ld_acquire_u32b(I.bar) < target) {
+                    const uint64_t t0 = globaltimer_ns();
+                    while (ld_acquire_u32b(I.bar) < target) {
+                        if (globaltimer_ns() - t0 > kTeamWaitNs) {
+                            good = 0;
+                            break;
+                        }
+                    }
+                }
+                flag[2] = good;
+            }
+            __syncthreads();
+            if (!flag[2]) ok = false;
+        };
+
+        // ---- statistics of the initial pass and the tolerances (fixed order; every member)
         if (warp == 0) {
             double sum = 0.0, mx = 0.0;
             for (int64_t j = lane; j < n; j += 32) {
@@ -231,23 +285,24 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
         int32_t stop = (st0 != ST_OK) ? STOP_BREAK : STOP_NONE;
         int64_t k = 0;
         // Y chunk geometry: the ring as two buffers of half its size, both planes per chunk
-        const int LC = (int)min((int64_t)kBMaxLC, (int64_t)(kBRingBytes / 8) / (2 * ldp));
+        const int LC = (int)min((int64_t)kBMaxLC, (int64_t)(kBRingBytes / 8) / (2 * rb));
         const int64_t buf_f = kBRingBytes / 8;  // floats per buffer
 
-        // streams Y columns [0, k) in chunks through the two ring buffers (consumer threads);
-        // stage(l, hi, lo) gives the coefficient of column l, body(yh, yl, ch, cl, l0, lc) runs on
-        // the chunk, post(l0, lc) after the barrier that closes it.  Every barrier is reached by
-        // all consumer threads whatever their waits returned.
+        // streams columns [0, k) of this member's Y block in chunks through the two ring buffers
+        // (consumer threads); stage(l, hi, lo) gives the coefficient of column l,
+        // body(yh, yl, ch, cl, l0, lc) runs on the chunk, post(l0, lc) after the barrier that
+        // closes it.  Every barrier is reached by all consumer threads whatever their waits
+        // returned.
         auto ystream = [&](auto&& stage, auto&& body, auto&& post) {
             const int64_t nch = ceil_div(k, (int64_t)LC);
             auto issue = [&](int64_t c) {
                 const int bf = (int)((ycount + (uint32_t)c) & 1u);
                 const int64_t l0 = c * LC;
                 const int lc = (int)min((int64_t)LC, k - l0);
-                const uint32_t bytes = (uint32_t)(lc * ldp * 4);
+                const uint32_t bytes = (uint32_t)(lc * rb * 4);
                 mbar_arrive_expect_tx(&ybar[bf], 2u * bytes);
-                bulk_g2s(ring + bf * buf_f, I.ys + l0 * ldp, bytes, &ybar[bf], pol_y);
-                bulk_g2s(ring + bf * buf_f + (int64_t)LC * ldp, I.ys + (dmax + l0) * ldp, bytes, &ybar[bf], pol_y);
+                bulk_g2s(ring + bf * buf_f, ysb + l0 * rb, bytes, &ybar[bf], pol_y);
+                bulk_g2s(ring + bf * buf_f + (int64_t)LC * rb, ysb + (dmax + l0) * rb, bytes, &ybar[bf], pol_y);
             };
             if (tid == 0 && nch > 0) issue(0);
             for (int64_t c = 0; c < nch; ++c) {
@@ -262,7 +317,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 named_bar(1, kBNCONS);
                 const uint32_t par = ((ycount + (uint32_t)c) >> 1) & 1u;
                 if (ok && !mbar_wait(&ybar[bf], par)) ok = false;
-                if (ok) body(ring + bf * buf_f, ring + bf * buf_f + (int64_t)LC * ldp, ch, cl, l0, lc);
+                if (ok) body(ring + bf * buf_f, ring + bf * buf_f + (int64_t)LC * rb, ch, cl, l0, lc);
                 named_bar(1, kBNCONS);
                 post(l0, lc);
             }
@@ -272,7 +327,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
 
         while (stop == STOP_NONE && ok) {
             if (warp < kBNW) {
-                // ---- O1: v1 = x_i - Y t for all rows (rows tid + kBNCONS q)
+                // ---- O1: v1 = x_i - Y t for this member's rows (tid + kBNCONS q)
                 float as[kBQR], ac[kBQR];
 #pragma unroll
                 for (int q = 0; q < kBQR; ++q) as[q] = ac[q] = 0.f;
@@ -282,17 +337,17 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                             [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
 #pragma unroll
                                 for (int q = 0; q < kBQR; ++q) {
-                                    const int64_t r = tid + (int64_t)kBNCONS * q;
-                                    if (r >= ldp) break;
+                                    const int64_t rr = tid + (int64_t)kBNCONS * q;
+                                    if (r_lo + rr >= r_hi) break;
                                     for (int l = 0; l < lc; ++l)
-                                        ff_mac2(as[q], ac[q], yh[l * ldp + r], yl[l * ldp + r], ch[l], cl[l]);
+                                        ff_mac2(as[q], ac[q], yh[l * rb + rr], yl[l * rb + rr], ch[l], cl[l]);
                                 }
                             },
                             nopost);
 #pragma unroll
                 for (int q = 0; q < kBQR; ++q) {
-                    const int64_t r = tid + (int64_t)kBNCONS * q;
-                    if (r >= ldp) break;
+                    const int64_t r = r_lo + tid + (int64_t)kBNCONS * q;
+                    if (r >= r_hi) break;
                     double v = 0.0;
                     if (r < m) {
                         const double x = (P == 2) ? ((const double*)I.X)[piv * I.ldx + r]
@@ -302,17 +357,18 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     split_double(v, vh[r], vl[r]);
                 }
                 named_bar(1, kBNCONS);
-                // ---- O1': h_l = Y(:, l)' v1 (per-thread rows, per-warp float-float sums, warps in order)
+                // ---- O1': h_l = Y(:, l)' v1 over this member's rows (per-warp float-float sums,
+                //      warps in order)
                 if (k > 0)
                     ystream([&](int64_t, float& hi, float& lo) { hi = lo = 0.f; },
-                            [&](const float* yh, const float* yl, const float*, const float*, int64_t l0, int lc) {
+                            [&](const float* yh, const float* yl, const float*, const float*, int64_t, int lc) {
                                 for (int l = 0; l < lc; ++l) {
                                     float s = 0.f, c = 0.f;
 #pragma unroll
                                     for (int q = 0; q < kBQR; ++q) {
-                                        const int64_t r = tid + (int64_t)kBNCONS * q;
-                                        if (r >= ldp) break;
-                                        ff_mac2(s, c, yh[l * ldp + r], yl[l * ldp + r], vh[r], vl[r]);
+                                        const int64_t rr = tid + (int64_t)kBNCONS * q;
+                                        if (r_lo + rr >= r_hi) break;
+                                        ff_mac2(s, c, yh[l * rb + rr], yl[l * rb + rr], vh[r_lo + rr], vl[r_lo + rr]);
                                     }
                                     warp_sum_ff(s, c);
                                     if (lane == 0) {
@@ -328,7 +384,24 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                                     hacc[l0 + l] = ff_to_double(s, c);
                                 }
                             });
-                // ---- O3: v2 = v1 - Y h, ||v2||^2
+            }
+            if (tm > 1 && k > 0) {
+                // the team's h: every member's partial sums, added in member order
+                __syncthreads();
+                if (warp < kBNW)
+                    for (int64_t l = tid; l < k; l += kBNCONS) I.hpart[mb * dmax + l] = hacc[l];
+                team_sync();
+                if (warp < kBNW)
+                    for (int64_t l = tid; l < k; l += kBNCONS) {
+                        double acc = 0.0;
+                        for (int b2 = 0; b2 < tm; ++b2) acc += __ldcg(&I.hpart[b2 * dmax + l]);
+                        hacc[l] = acc;
+                    }
+                __syncthreads();
+            }
+            if (warp < kBNW) {
+                // ---- O3: v2 = v1 - Y h on this member's rows, ||v2||^2
+                float as[kBQR], ac[kBQR];
 #pragma unroll
                 for (int q = 0; q < kBQR; ++q) as[q] = ac[q] = 0.f;
                 if (k > 0)
@@ -336,21 +409,25 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                             [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
 #pragma unroll
                                 for (int q = 0; q < kBQR; ++q) {
-                                    const int64_t r = tid + (int64_t)kBNCONS * q;
-                                    if (r >= ldp) break;
+                                    const int64_t rr = tid + (int64_t)kBNCONS * q;
+                                    if (r_lo + rr >= r_hi) break;
                                     for (int l = 0; l < lc; ++l)
-                                        ff_mac2(as[q], ac[q], yh[l * ldp + r], yl[l * ldp + r], ch[l], cl[l]);
+                                        ff_mac2(as[q], ac[q], yh[l * rb + rr], yl[l * rb + rr], ch[l], cl[l]);
                                 }
                             },
                             nopost);
                 double nrm = 0.0;
 #pragma unroll
                 for (int q = 0; q < kBQR; ++q) {
-                    const int64_t r = tid + (int64_t)kBNCONS * q;
-                    if (r >= ldp) break;
+                    const int64_t r = r_lo + tid + (int64_t)kBNCONS * q;
+                    if (r >= r_hi) break;
                     double v = 0.0;
                     if (r < m) v = ((double)vh[r] + (double)vl[r]) - ff_to_double(as[q], ac[q]);
                     split_double(v, vh[r], vl[r]);  // v2 replaces v1 (each thread owns its rows)
+                    if (tm > 1) {
+                        I.vbuf[r] = vh[r];
+                        I.vbuf[ldp + r] = vl[r];
+                    }
                     nrm += v * v;
                 }
                 nrm = warp_sum_double(nrm);
@@ -358,11 +435,32 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
             }
             ok = __syncthreads_and(ok) != 0;
             if (!ok) break;
-            // ---- nu, certified E_cur of basis k-1, stop tests of steps 2.2 / 2.4
             if (tid == 0) {
                 double acc = 0.0;
                 for (int w = 0; w < kBNW; ++w) acc += red[w];
-                const double nuv = sqrt(acc);
+                bc[2] = acc;
+                if (tm > 1) I.nrm[mb] = acc;
+            }
+            if (tm > 1) {
+                team_sync();  // every member's rows of v2 and ||v2||^2 are out
+                if (tid == 0) {
+                    double acc = 0.0;
+                    for (int b2 = 0; b2 < tm; ++b2) acc += __ldcg(&I.nrm[b2]);
+                    bc[2] = acc;
+                }
+                // the other members' rows of v2
+                if (warp < kBNW)
+                    for (int64_t r = tid; r < ldp; r += kBNCONS)
+                        if (r < r_lo || r >= r_hi) {
+                            vh[r] = __ldcg(&I.vbuf[r]);
+                            vl[r] = __ldcg(&I.vbuf[ldp + r]);
+                        }
+            }
+            __syncthreads();
+            // ---- nu, certified E_cur of basis k-1, stop tests of steps 2.2 / 2.4 (identical in
+            //      every member; member 0 writes the outputs)
+            if (tid == 0) {
+                const double nuv = sqrt(bc[2]);
                 const double xin = sqrt(__ldcg(&I.xn2[piv]));
                 int32_t st = STOP_NONE;
                 if (k > 0) {
@@ -374,41 +472,42 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 }
                 if (st == STOP_NONE && k >= dmax) st = STOP_DMAX;
                 if (st == STOP_NONE && (nuv < eps_r22 || nuv <= kRankFloor * xin)) st = STOP_BREAK;
-                if (k > 0) I.err[k - 1] = nuv;
-                if (st == STOP_NONE) {
-                    I.piv[k] = piv;
-                    if (I.nu) I.nu[k] = nuv;
+                if (mb == 0) {
+                    if (k > 0) I.err[k - 1] = nuv;
+                    if (st == STOP_NONE) {
+                        I.piv[k] = piv;
+                        if (I.nu) I.nu[k] = nuv;
+                    }
                 }
-                bc[2] = nuv;
+                bc[3] = nuv;
                 flag[1] = st;
             }
             __syncthreads();
-            const double nuv = bc[2];
+            const double nuv = bc[3];
             if (k > 0) err_last = nuv;
             stop = flag[1];
             if (stop != STOP_NONE) break;
 
-            // ---- xi = v2 / nu: Y(:, k), its split copy, and the pass vector in shared memory
+            // ---- xi = v2 / nu: the whole vector for the pass; this member's rows of Y(:, k)
             const double inv_nu = 1.0 / nuv;
             if (warp < kBNW) {
-#pragma unroll
-                for (int q = 0; q < kBQR; ++q) {
-                    const int64_t r = tid + (int64_t)kBNCONS * q;
-                    if (r >= ldp) break;
+                for (int64_t r = tid; r < ldp; r += kBNCONS) {
                     const double y = ((double)vh[r] + (double)vl[r]) * inv_nu;
-                    if (r < m) I.Y[r + k * I.ldy] = y;
                     split_double(y, vh[r], vl[r]);
-                    I.ys[k * ldp + r] = vh[r];
-                    I.ys[(dmax + k) * ldp + r] = vl[r];
+                    if (r >= r_lo && r < r_hi) {
+                        if (r < m) I.Y[r + k * I.ldy] = y;
+                        I.ys[((int64_t)mb * 2 * dmax + k) * rb + (r - r_lo)] = vh[r];
+                        I.ys[((int64_t)mb * 2 * dmax + dmax + k) * rb + (r - r_lo)] = vl[r];
+                    }
                 }
                 fence_proxy_async_global();  // Y's split copy is read by bulk copies later
             }
             __syncthreads();
 
-            // ---- the fused pass
+            // ---- the fused pass over this member's column groups
             if (warp == kBNW) {
                 if (lane == 0 && ok) {
-                    int64_t g = 0, t = 0;
+                    int64_t g = g_lo, t = 0;
                     for (int64_t u = 0; u < W; ++u) {
                         if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
                             ok = false;
@@ -439,7 +538,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 double best_e = -1.0, esum = 0.0;
                 int64_t best_j = INT64_MAX;
                 double e_old[kBCPW] = {0.0, 0.0};
-                int64_t g = 0, t = 0;
+                int64_t g = g_lo, t = 0;
                 for (int64_t u = 0; u < W; ++u) {
                     const int s = cs;
                     const uint32_t ph = cph;
@@ -504,7 +603,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
             }
             ok = __syncthreads_and(ok) != 0;
             if (!ok) break;
-            // ---- argmax over the warps, Frobenius residual (fixed order)
+            // ---- argmax over the warps (and the team's members), Frobenius residual (fixed order)
             if (tid == 0) {
                 double be = -1.0, fs = 0.0;
                 int64_t bj = INT64_MAX;
@@ -515,17 +614,46 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     }
                     fs += red[kBNW + w];
                 }
-                bc[3] = sqrt(fmax(fs, 0.0));
+                bc[4] = be;
+                bc[5] = fs;
+                redj[kBNW] = bj;
+                if (tm > 1) {
+                    I.cand_e[mb] = be;
+                    I.cand_j[mb] = bj;
+                    I.frop[mb] = fs;
+                }
+            }
+            if (tm > 1) {
+                team_sync();
+                if (tid == 0) {
+                    double be = -1.0, fs = 0.0;
+                    int64_t bj = INT64_MAX;
+                    for (int b2 = 0; b2 < tm; ++b2) {
+                        const double ce = __ldcg(&I.cand_e[b2]);
+                        const int64_t cj = __ldcg(reinterpret_cast<const long long*>(&I.cand_j[b2]));
+                        if (better(ce, cj, be, bj)) {
+                            be = ce;
+                            bj = cj;
+                        }
+                        fs += __ldcg(&I.frop[b2]);
+                    }
+                    bc[5] = fs;
+                    redj[kBNW] = bj;
+                }
+            }
+            if (tid == 0) {
+                const int64_t bj = redj[kBNW];
+                bc[6] = sqrt(fmax(bc[5], 0.0));
                 redj[kBNW] = (bj >= 0 && bj < n) ? bj : piv;
             }
             __syncthreads();
-            fro_prev = bc[3];
+            fro_prev = bc[6];
             piv = redj[kBNW];
             ++k;
-            __syncthreads();
+            ok = __syncthreads_and(ok) != 0;
         }
-        // ---- result of this matrix
-        if (tid == 0) {
+        // ---- result of this matrix (member 0)
+        if (tid == 0 && mb == 0) {
             rbd_batch_result rr;
             rr.d = k;
             rr.next_pivot = piv;
@@ -555,16 +683,18 @@ size_t batch_smem() {
 struct rbd_batch_plan_s {
     int xt = 0;
     int64_t count = 0;
+    int64_t nslots = 0;
     int S = 0;
     int num_sms = 0;
     size_t smem = 0;
     int init_blocks = 0;
     rbd::BInst* d_inst = nullptr;
-    int32_t* d_order = nullptr;
+    int32_t* d_slot_inst = nullptr;
+    int32_t* d_slot_member = nullptr;
     int64_t* d_colstart = nullptr;
-    uint32_t* d_queue = nullptr;  // followed by the status array (count int32)
+    uint32_t* d_queue = nullptr;
     int32_t* d_status = nullptr;
-    size_t zero_bytes = 0;
+    size_t zero_bytes = 0;  // queue, statuses and team barrier counters
 };
 
 using namespace rbd;
@@ -572,11 +702,6 @@ using namespace rbd;
 namespace {
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
-
-struct Layout {
-    size_t inst, order, colstart, queue, status, per_begin, total;
-    std::vector<size_t> planes, ys, e, xn2;
-};
 
 rbd_status check_inst(const rbd_instance& I, rbd_dtype xt) {
     if (!I.X || !I.Y || !I.T || !I.pivots || !I.err) return RBD_EINVAL;
@@ -591,7 +716,53 @@ rbd_status check_inst(const rbd_instance& I, rbd_dtype xt) {
     return RBD_OK;
 }
 
-bool make_layout(const rbd_instance* inst, int64_t count, rbd_dtype xt, Layout& L) {
+// Team sizes: a matrix whose estimated work (passes over X for its expected number of bases -- the
+// caller's hint, else d_max -- plus the Gram-Schmidt streams) exceeds 2/3 of a CTA's fair share of
+// the batch gets ceil(1.5 work / share) members, at most 16, one column group and 128 rows per
+// member.
+struct Plan {
+    std::vector<int32_t> team;
+    std::vector<int64_t> rb;
+    std::vector<double> cost;
+    std::vector<int32_t> order;  // matrices by decreasing cost
+    int64_t nslots = 0;
+};
+
+Plan make_plan(const rbd_instance* inst, int64_t count, int P, int ctas) {
+    Plan pl;
+    pl.team.resize(count);
+    pl.rb.resize(count);
+    pl.cost.resize(count);
+    double total = 0.0;
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t dh = inst[i].d_hint > 0 ? std::min<int64_t>(inst[i].d_hint, inst[i].d_max) : inst[i].d_max;
+        const double ldp = (double)round_up(inst[i].m, 128), n = (double)inst[i].n, d = (double)dh;
+        pl.cost[i] = ldp * n * P * d + 3.0 * ldp * d * d;
+        total += pl.cost[i];
+    }
+    const double share = total / std::max(1, ctas);
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t ldp = round_up(inst[i].m, 128);
+        const int64_t ng = ceil_div(inst[i].n, (int64_t)kBC);
+        const int64_t tmax = std::max<int64_t>(1, std::min<int64_t>({16, ng, ldp / 128}));
+        int64_t t = (int64_t)std::ceil(1.5 * pl.cost[i] / share);
+        t = std::max<int64_t>(1, std::min(t, tmax));
+        pl.team[i] = (int32_t)t;
+        pl.rb[i] = round_up(ceil_div(ldp, t), 32);
+        pl.nslots += t;
+    }
+    pl.order.resize(count);
+    std::iota(pl.order.begin(), pl.order.end(), 0);
+    std::stable_sort(pl.order.begin(), pl.order.end(), [&](int32_t a, int32_t b) { return pl.cost[a] > pl.cost[b]; });
+    return pl;
+}
+
+struct Layout {
+    size_t queue, status, bars, per_begin, inst, slot_inst, slot_member, colstart, total;
+    std::vector<size_t> planes, ys, e, xn2, hpart, nrm, vbuf, cand_e, cand_j, frop;
+};
+
+bool make_layout(const rbd_instance* inst, int64_t count, rbd_dtype xt, const Plan& pl, Layout& L) {
     const int P = (xt == RBD_F64) ? 2 : 1;
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -601,22 +772,31 @@ bool make_layout(const rbd_instance* inst, int64_t count, rbd_dtype xt, Layout& 
     };
     L.queue = take(4);
     L.status = take((size_t)count * 4);
+    L.bars = take((size_t)count * 4);
     L.per_begin = off;
     L.inst = take((size_t)count * sizeof(BInst));
-    L.order = take((size_t)count * 4);
+    L.slot_inst = take((size_t)pl.nslots * 4);
+    L.slot_member = take((size_t)pl.nslots * 4);
     L.colstart = take((size_t)(count + 1) * 8);
-    L.planes.resize(count);
-    L.ys.resize(count);
-    L.e.resize(count);
-    L.xn2.resize(count);
+    for (auto* v : {&L.planes, &L.ys, &L.e, &L.xn2, &L.hpart, &L.nrm, &L.vbuf, &L.cand_e, &L.cand_j, &L.frop})
+        v->assign(count, 0);
     for (int64_t i = 0; i < count; ++i) {
         if (check_inst(inst[i], xt) != RBD_OK) return false;
         const int64_t ldp = round_up(inst[i].m, 128);
         const int64_t ng = ceil_div(inst[i].n, (int64_t)kBC);
+        const int64_t t = pl.team[i];
         L.planes[i] = take((size_t)ng * kBC * P * ldp * 4);
-        L.ys[i] = take((size_t)2 * inst[i].d_max * ldp * 4);
+        L.ys[i] = take((size_t)t * 2 * inst[i].d_max * pl.rb[i] * 4);
         L.e[i] = take((size_t)inst[i].n * 8);
         L.xn2[i] = take((size_t)inst[i].n * 8);
+        if (t > 1) {
+            L.hpart[i] = take((size_t)t * inst[i].d_max * 8);
+            L.nrm[i] = take((size_t)t * 8);
+            L.vbuf[i] = take((size_t)2 * ldp * 4);
+            L.cand_e[i] = take((size_t)t * 8);
+            L.cand_j[i] = take((size_t)t * 8);
+            L.frop[i] = take((size_t)t * 8);
+        }
     }
     L.total = off;
     return true;
@@ -642,11 +822,22 @@ cudaError_t batch_setup(int dev) {
     return e;
 }
 
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms;
+}
+
 rbd_status run_with(rbd_batch_plan p, rbd_batch_result* results, cudaStream_t st, int S) {
     BatchParams bp;
     bp.inst = p->d_inst;
     bp.count = p->count;
-    bp.order = p->d_order;
+    bp.nslots = p->nslots;
+    bp.slot_inst = p->d_slot_inst;
+    bp.slot_member = p->d_slot_member;
     bp.colstart = p->d_colstart;
     bp.queue = p->d_queue;
     bp.status = p->d_status;
@@ -654,20 +845,19 @@ rbd_status run_with(rbd_batch_plan p, rbd_batch_result* results, cudaStream_t st
     bp.S = S;
     cudaError_t e = cudaMemsetAsync(p->d_queue, 0, p->zero_bytes, st);
     if (e != cudaSuccess) return cuda_status(e);
+    void* args[] = {&bp};
     if (p->xt == RBD_F64) {
         batch_init_kernel<2><<<p->init_blocks, 256, 0, st>>>(bp);
         e = cudaGetLastError();
-        if (e == cudaSuccess) {
-            batch_kernel<2><<<p->num_sms, kBThreads, p->smem, st>>>(bp);
-            e = cudaGetLastError();
-        }
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel((const void*)batch_kernel<2>, dim3((unsigned)p->num_sms), dim3(kBThreads), args,
+                                            p->smem, st);
     } else {
         batch_init_kernel<1><<<p->init_blocks, 256, 0, st>>>(bp);
         e = cudaGetLastError();
-        if (e == cudaSuccess) {
-            batch_kernel<1><<<p->num_sms, kBThreads, p->smem, st>>>(bp);
-            e = cudaGetLastError();
-        }
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel((const void*)batch_kernel<1>, dim3((unsigned)p->num_sms), dim3(kBThreads), args,
+                                            p->smem, st);
     }
     return cuda_status(e);
 }
@@ -678,8 +868,13 @@ extern "C" {
 
 size_t rbd_batch_workspace_bytes(const rbd_instance* inst, int64_t count, rbd_dtype xt) {
     if (!inst || count < 1) return 0;
+    for (int64_t i = 0; i < count; ++i)
+        if (check_inst(inst[i], xt) != RBD_OK) return 0;
+    int sms = device_sms();
+    if (sms <= 0) sms = 160;  // no device: plan for a 160-SM part
+    const Plan pl = make_plan(inst, count, (xt == RBD_F64) ? 2 : 1, sms);
     Layout L;
-    if (!make_layout(inst, count, xt, L)) return 0;
+    if (!make_layout(inst, count, xt, pl, L)) return 0;
     return L.total;
 }
 
@@ -691,25 +886,27 @@ rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst,
         const rbd_status s = check_inst(inst[i], xt);
         if (s != RBD_OK) return s;
     }
-    Layout L;
-    if (!make_layout(inst, count, xt, L)) return RBD_EINVAL;
-    if (!workspace || ((uintptr_t)workspace & 255u) != 0) return RBD_EINVAL;
-    if (workspace_bytes < L.total) return RBD_ENOMEM;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_status(ce);
-    int sms = 0;
+    int sms = 0, coop = 0;
     ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (ce == cudaSuccess) ce = batch_setup(dev);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return cuda_status(ce);
     }
+    if (!coop) return RBD_EUNSUPPORTED;
     const int P = (xt == RBD_F64) ? 2 : 1;
+    const Plan pl = make_plan(inst, count, P, sms);
+    Layout L;
+    if (!make_layout(inst, count, xt, pl, L)) return RBD_EINVAL;
+    if (!workspace || ((uintptr_t)workspace & 255u) != 0) return RBD_EINVAL;
+    if (workspace_bytes < L.total) return RBD_ENOMEM;
     unsigned char* base = (unsigned char*)workspace;
     std::vector<BInst> hi(count);
     std::vector<int64_t> colstart(count + 1, 0);
-    std::vector<double> cost(count);
     for (int64_t i = 0; i < count; ++i) {
         const rbd_instance& s = inst[i];
         BInst& b = hi[i];
@@ -723,6 +920,7 @@ rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst,
         b.NT = ceil_div(b.ldp, (int64_t)kBMT);
         b.tol = s.tol;
         b.mode = s.mode;
+        b.team = pl.team[i];
         b.d_max = s.d_max;
         b.start = s.start;
         b.Y = s.Y;
@@ -734,19 +932,34 @@ rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst,
         b.nu = s.nu;
         b.planes = (float*)(base + L.planes[i]);
         b.ys = (float*)(base + L.ys[i]);
+        b.rb = pl.rb[i];
         b.e = (double*)(base + L.e[i]);
         b.xn2 = (double*)(base + L.xn2[i]);
+        b.bar = (uint32_t*)(base + L.bars) + i;
+        if (pl.team[i] > 1) {
+            b.hpart = (double*)(base + L.hpart[i]);
+            b.nrm = (double*)(base + L.nrm[i]);
+            b.vbuf = (float*)(base + L.vbuf[i]);
+            b.cand_e = (double*)(base + L.cand_e[i]);
+            b.cand_j = (int64_t*)(base + L.cand_j[i]);
+            b.frop = (double*)(base + L.frop[i]);
+        }
         colstart[i + 1] = colstart[i] + b.ngroups * kBC;
-        cost[i] = (double)b.ldp * (double)b.n * (double)P * (double)std::min<int64_t>(s.d_max, 64) +
-                  (double)b.ldp * (double)s.d_max * (double)s.d_max;
     }
-    std::vector<int32_t> order(count);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    std::vector<int32_t> slot_inst, slot_member;
+    slot_inst.reserve(pl.nslots);
+    slot_member.reserve(pl.nslots);
+    for (int32_t i : pl.order)
+        for (int32_t b = 0; b < pl.team[i]; ++b) {
+            slot_inst.push_back(i);
+            slot_member.push_back(b);
+        }
     cudaStream_t st = (cudaStream_t)stream;
     ce = cudaMemcpyAsync(base + L.inst, hi.data(), (size_t)count * sizeof(BInst), cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(base + L.order, order.data(), (size_t)count * 4, cudaMemcpyHostToDevice, st);
+        ce = cudaMemcpyAsync(base + L.slot_inst, slot_inst.data(), (size_t)pl.nslots * 4, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(base + L.slot_member, slot_member.data(), (size_t)pl.nslots * 4, cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(base + L.colstart, colstart.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // the host vectors go out of scope
@@ -758,12 +971,14 @@ rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst,
     if (!p) return RBD_ENOMEM;
     p->xt = (int)xt;
     p->count = count;
+    p->nslots = pl.nslots;
     p->S = (P == 2) ? BCfg<2>::SMAX : BCfg<1>::SMAX;
     p->num_sms = sms;
     p->smem = (P == 2) ? batch_smem<2>() : batch_smem<1>();
     p->init_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(colstart[count], 8), (int64_t)sms * 8));
     p->d_inst = (BInst*)(base + L.inst);
-    p->d_order = (int32_t*)(base + L.order);
+    p->d_slot_inst = (int32_t*)(base + L.slot_inst);
+    p->d_slot_member = (int32_t*)(base + L.slot_member);
     p->d_colstart = (int64_t*)(base + L.colstart);
     p->d_queue = (uint32_t*)(base + L.queue);
     p->d_status = (int32_t*)(base + L.status);

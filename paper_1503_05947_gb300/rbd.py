@@ -48,7 +48,7 @@ class _Profile(ctypes.Structure):
 
 class _Instance(ctypes.Structure):
     _fields_ = [("X", _PTR), ("m", _I64), ("n", _I64), ("ldx", _I64), ("tol", _DBL), ("mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("d_max", _I64), ("start", _I64), ("Y", _PTR), ("ldy", _I64),
+                ("d_hint", ctypes.c_int32), ("d_max", _I64), ("start", _I64), ("Y", _PTR), ("ldy", _I64),
                 ("T", _PTR), ("ldt", _I64), ("pivots", _PTR), ("err", _PTR), ("nu", _PTR)]
 
 
@@ -345,7 +345,8 @@ class BatchPlan:
     """The batched form: many column-major CUDA matrices of one dtype (float64 or float32), each
     with its own tolerance, mode, d_max and start column, compressed in one persistent launch.
 
-    ``items`` is a list of dicts {X, tol, d_max, tol_mode="maxcol_abs", start=0}.  The plan owns the
+    ``items`` is a list of dicts {X, tol, d_max, tol_mode="maxcol_abs", start=0, d_hint=0}; d_hint,
+    the expected number of bases, only orders the queue and sizes teams of CTAs.  The plan owns the
     outputs (per matrix Y, T, pivots, err, nu), the workspace and the device result array.
     ``run()`` only enqueues work on the current stream (capturable in a CUDA graph);
     ``results()`` synchronises and returns the per-matrix summaries; ``compressed(i)`` the outputs
@@ -377,7 +378,8 @@ class BatchPlan:
                  "nu": torch.empty(d_max, dtype=torch.float64, device=self.device)}
             self.out.append(o)
             inst[i] = _Instance(X.data_ptr(), m, n, ldx, float(it.get("tol", 0.0)),
-                                TOL_MODES[it.get("tol_mode", "maxcol_abs")], 0, d_max, int(it.get("start", 0)),
+                                TOL_MODES[it.get("tol_mode", "maxcol_abs")], int(it.get("d_hint", 0)), d_max,
+                                int(it.get("start", 0)),
                                 o["Y"].data_ptr(), m, o["T"].data_ptr(), d_max, o["pivots"].data_ptr(),
                                 o["err"].data_ptr(), o["nu"].data_ptr())
         self._inst = inst

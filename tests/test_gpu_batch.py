@@ -152,7 +152,8 @@ def test_batched_workload_2048_sampled(rbd, oracle_mod):
     for sp in specs:
         s = gen.decay_spectrum(sp["rate"], min(sp["m"], sp["n"]))
         X = gen.lowrank_torch(sp["m"], sp["n"], s, sp["seed"], device="cuda", dtype=torch.float32)
-        items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"]})
+        items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"],
+                          "d_hint": sp["d_hint"]})
     plan = rbd.BatchPlan(items)
     plan.run()
     res = plan.results()
