@@ -60,7 +60,7 @@ struct Ctl {
     int32_t mode;         // MODE_*
     int32_t pad1;
     int64_t d_max;
-    uint32_t bar[2];      // grid barrier of the persistent loop kernel {arrivals, generation}
+    uint32_t bar[2];      // grid barrier of the persistent loop kernel: {arrivals (monotonic), unused}
 };
 
 // Element idx of X stored as FP64 (xt 0), FP32 (1) or BF16 (2), widened exactly to FP64.

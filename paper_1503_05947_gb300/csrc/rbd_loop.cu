@@ -127,32 +127,26 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
     return v;
 }
 
-__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid-wide barrier for a cooperative launch; called by every thread of every CTA.  Returns
-// false in all threads of a CTA whose wait ran out (the caller then leaves the loop).
+// Grid-wide barrier for a cooperative launch; called by every thread of every CTA.  The arrival
+// counter only grows: the barrier with index gen (1, 2, ...) is passed once it reaches
+// nblocks * gen, so no CTA has to reset it and the last arrival needs no extra release step.
+// Returns false in all threads of a CTA whose wait ran out (the caller then leaves the loop).
 __device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint32_t& gen, int* s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const uint32_t my = gen;
-        __threadfence();
-        if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            st_release_u32(&bar[1], my + 1);
-        } else {
+        const uint32_t target = nblocks * (++gen);
+        uint32_t seen;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(seen) : "l"(bar) : "memory");
+        if (seen + 1 < target) {
             const uint64_t t0 = globaltimer_ns();
-            while (ld_acquire_u32(&bar[1]) == my) {
+            while (ld_acquire_u32(bar) < target) {
                 if (globaltimer_ns() - t0 > kBarrierLimitNs) {
                     ok = 0;
                     break;
                 }
             }
         }
-        gen = my + 1;
         *s_ok = ok;
     }
     __syncthreads();
