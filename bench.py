@@ -259,7 +259,7 @@ def run_gpu(args, world, rank, local):
                 loop_passes += pf["pass_launches"]
             init_ms += pf["init_ms"]
             passes_total += r.d + 1
-            launches += r.launches + 1
+            launches += r.launches + 2  # + the projection: row-split partial products and their sum
         e1.record(stream)
         torch.cuda.synchronize(dev)
     barrier(world)

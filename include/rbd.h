@@ -189,7 +189,10 @@ rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t m, int64_t 
  *  Y  [in]  device, m x d FP64 column-major, ldy >= m (orthonormal columns from rbd_compress).
  *  V  [in]  device, m x k column-major, ldv >= m, storage type vt.
  *  C  [out] device, d x k FP64 column-major, ldc >= d.
- *  d = 0 or k = 0 is a no-op.  Stream-ordered; does not synchronise.  Dot products are
+ *  d = 0 or k = 0 is a no-op.  Stream-ordered; does not synchronise.  For tall Y the rows are
+ *  split across CTAs and a stream-ordered scratch of (splits x d x k) doubles holds the partial
+ *  products (allocated with cudaMallocAsync and freed on the stream; if that allocation fails the
+ *  rows are not split).  Dot products are
  *  evaluated with FP64-grade (float-float, relative error below 2^-44) accuracy.
  *  Errors: RBD_EINVAL for bad sizes/leading dimensions/NULL; RBD_ECUDA on launch failure.
  */

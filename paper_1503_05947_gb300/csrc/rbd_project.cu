@@ -1,9 +1,12 @@
 // rbd_project.cu -- the out-of-sample map of Section 3.1, v_C = Y' v (Section 3.3 "Online":
 // cost m d per vector), for a block of k vectors: C = Y' V.
 //
-// Each CTA owns a 32 x 32 tile of C and walks the m rows in 32-row chunks staged in shared
-// memory, split into float-float form on load; each thread accumulates 4 outputs over all m
-// rows in order (deterministic), FP64-grade accuracy on the FP32 pipes.
+// Each CTA owns a 32 x 32 tile of C and a range of rows, walked in 32-row chunks staged in shared
+// memory and split into float-float form on load; each thread accumulates 4 outputs over its rows
+// in order.  Tall Y are split into row ranges (enough CTAs to fill the GPU) whose partial tiles a
+// second kernel adds in range order: deterministic, FP64-grade accuracy on the FP32 pipes.
+#include <algorithm>
+
 #include "rbd_device.cuh"
 #include "rbd_work.h"
 
@@ -27,23 +30,25 @@ __device__ __forceinline__ double load_v(const void* V, int vt, int64_t idx) {
 
 constexpr int kPT = 32;  // tile edge
 
-// grid (ceil(d/32), ceil(k/32)), 256 threads; thread (ty = tid / 8, tx = tid % 8) computes
-// C(l0 + ty, c0 + tx + 8 q), q = 0..3.
-__global__ void __launch_bounds__(256) project_kernel(ProjParams p) {
+// grid (ceil(d/32), ceil(k/32), nsplit), 256 threads; thread (ty = tid / 8, tx = tid % 8) computes
+// C(l0 + ty, c0 + tx + 8 q), q = 0..3, over rows [z * rows_per, (z + 1) * rows_per).  With one
+// split it writes C; with several it writes its partial tile to part[z] (FP64, d x k, ld d).
+__global__ void __launch_bounds__(256) project_kernel(ProjParams p, int64_t rows_per, double* part) {
     __shared__ float yh[kPT][kPT + 1], yl[kPT][kPT + 1];   // [row][basis]
     __shared__ float vh[kPT][kPT + 1], vl[kPT][kPT + 1];   // [row][vector]
     const int tid = threadIdx.x;
     const int ty = tid >> 3, tx = tid & 7;
     const int64_t l0 = (int64_t)blockIdx.x * kPT, c0 = (int64_t)blockIdx.y * kPT;
+    const int64_t rbeg = (int64_t)blockIdx.z * rows_per, rend = min(p.m, rbeg + rows_per);
     float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t r0 = 0; r0 < p.m; r0 += kPT) {
+    for (int64_t r0 = rbeg; r0 < rend; r0 += kPT) {
         // stage a 32-row chunk of Y(:, l0:l0+32) and V(:, c0:c0+32); element (row, col) is
         // loaded by thread (col * 32 + row) % 256 four times over.
         for (int idx = tid; idx < kPT * kPT; idx += 256) {
             const int row = idx % kPT, col = idx / kPT;
             const int64_t r = r0 + row;
             double y = 0.0, v = 0.0;
-            if (r < p.m) {
+            if (r < rend) {
                 if (l0 + col < p.d) y = p.Y[(l0 + col) * p.ldy + r];
                 if (c0 + col < p.k) v = load_v(p.V, p.vt, (c0 + col) * p.ldv + r);
             }
@@ -69,17 +74,59 @@ __global__ void __launch_bounds__(256) project_kernel(ProjParams p) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t col = c0 + tx + 8 * q;
-            if (col < p.k) p.C[col * p.ldc + l] = ff_to_double(s[q], c[q]);
+            if (col >= p.k) continue;
+            if (part)
+                part[((int64_t)blockIdx.z * p.k + col) * p.d + l] = ff_to_double(s[q], c[q]);
+            else
+                p.C[col * p.ldc + l] = ff_to_double(s[q], c[q]);
         }
+    }
+}
+
+// C = sum of the row splits' partial products, in split order.
+__global__ void __launch_bounds__(256) project_reduce_kernel(ProjParams p, int nsplit, const double* part) {
+    const int64_t total = p.d * p.k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = i % p.d, col = i / p.d;
+        double acc = 0.0;
+        for (int z = 0; z < nsplit; ++z) acc += part[((int64_t)z * p.k + col) * p.d + l];
+        p.C[col * p.ldc + l] = acc;
     }
 }
 
 cudaError_t launch_project(const double* Y, int64_t m, int64_t d, int64_t ldy, const void* V, int vt,
                            int64_t k, int64_t ldv, double* C, int64_t ldc, cudaStream_t st) {
     ProjParams p{Y, m, d, ldy, V, vt, k, ldv, C, ldc};
-    dim3 grid((unsigned)ceil_div(d, kPT), (unsigned)ceil_div(k, kPT));
-    project_kernel<<<grid, 256, 0, st>>>(p);
-    return cudaGetLastError();
+    const int64_t tiles = ceil_div(d, (int64_t)kPT) * ceil_div(k, (int64_t)kPT);
+    // split the rows so that the grid covers the GPU twice over, each split at least 256 rows
+    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(ceil_div(2 * 152, tiles), m / 256));
+    nsplit = std::min<int64_t>(nsplit, 64);
+    const int64_t rows_per = round_up(ceil_div(m, nsplit), (int64_t)kPT);
+    nsplit = ceil_div(m, rows_per);
+    double* part = nullptr;
+    if (nsplit > 1) {
+        cudaError_t e = cudaMallocAsync((void**)&part, (size_t)nsplit * d * k * 8, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            part = nullptr;
+            nsplit = 1;
+        }
+    }
+    const int64_t rp = (nsplit > 1) ? rows_per : m;
+    dim3 grid((unsigned)ceil_div(d, (int64_t)kPT), (unsigned)ceil_div(k, (int64_t)kPT), (unsigned)nsplit);
+    project_kernel<<<grid, 256, 0, st>>>(p, rp, part);
+    cudaError_t e = cudaGetLastError();
+    if (part) {
+        if (e == cudaSuccess) {
+            const int64_t total = d * k;
+            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, (int64_t)256), 4096));
+            project_reduce_kernel<<<blocks, 256, 0, st>>>(p, (int)nsplit, part);
+            e = cudaGetLastError();
+        }
+        cudaError_t fe = cudaFreeAsync(part, st);
+        if (e == cudaSuccess) e = fe;
+    }
+    return e;
 }
 
 }  // namespace rbd
