@@ -201,6 +201,22 @@ rbd_status rbd_project(const double* Y, int64_t m, int64_t d, int64_t ldy,
                        double* C, int64_t ldc, void* stream);
 
 /*
+ * rbd_reconstruct -- "Uncompress" of Section 3.1: Xr = Y T, i.e. column j of the approximation
+ * of X is Y T(:, j) (and Y c for a compressed out-of-sample vector c = rbd_project's output).
+ *
+ *  Y   [in]  device, m x d FP64 column-major, ldy >= m.
+ *  T   [in]  device, d x n FP64 column-major, ldt >= d (pass T + j0 * ldt for columns j0..).
+ *  Xr  [out] device, m x n FP64 column-major, ldxr >= m.
+ *  d = 0 writes zeros; n = 0 is a no-op.  Stream-ordered; does not synchronise.  Sums over the d
+ *  bases are evaluated in order with FP64-grade (float-float) accuracy.
+ *  Errors: RBD_EINVAL for bad sizes, leading dimensions or NULL pointers; RBD_ECUDA on launch
+ *  failure.
+ */
+rbd_status rbd_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy,
+                           const double* T, int64_t n, int64_t ldt,
+                           double* Xr, int64_t ldxr, void* stream);
+
+/*
  * Batched form (an extension: the paper compresses one matrix at a time): many independent
  * matrices, each with its own sizes, tolerance and outputs, compressed by Algorithm 1 in ONE
  * persistent launch.  The plan orders the matrices by estimated work (m n d, with d the hint or

@@ -16,6 +16,7 @@ from .rbd import (  # noqa: F401
     get_profile,
     load,
     project,
+    reconstruct,
     set_profiling,
     status_string,
     version,

@@ -588,6 +588,17 @@ rbd_status rbd_project(const double* Y, int64_t m, int64_t d, int64_t ldy, const
     return map_cuda(ce);
 }
 
+rbd_status rbd_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy, const double* T, int64_t n,
+                           int64_t ldt, double* Xr, int64_t ldxr, void* stream) {
+    if (m < 1 || d < 0 || n < 0) return RBD_EINVAL;
+    if (n == 0) return RBD_OK;
+    if (!Xr || ldxr < m) return RBD_EINVAL;
+    if (d > 0 && (!Y || !T || ldy < m || ldt < d)) return RBD_EINVAL;
+    if (m > (int64_t(1) << 40) || n > (int64_t(1) << 31) || d > (int64_t(1) << 30)) return RBD_EUNSUPPORTED;
+    if (ceil_div(m, (int64_t)32) > (int64_t(1) << 31) - 1) return RBD_EUNSUPPORTED;
+    return map_cuda(launch_reconstruct(Y, m, d, ldy, T, n, ldt, Xr, ldxr, (cudaStream_t)stream));
+}
+
 void rbd_set_profiling(int enabled) { g_profiling.store(enabled ? 1 : 0); }
 
 rbd_status rbd_get_profile(rbd_profile* out) {

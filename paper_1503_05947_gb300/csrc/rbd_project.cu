@@ -130,3 +130,70 @@ cudaError_t launch_project(const double* Y, int64_t m, int64_t d, int64_t ldy, c
 }
 
 }  // namespace rbd
+
+namespace rbd {
+
+// ---------------------------------------------------------------------------------------------
+// Uncompress (Section 3.1): Xr = Y T, column j of the approximation = Y T(:, j) (Section 3.3:
+// m d per column).  Each CTA owns a 32 x 32 tile of Xr and walks the d bases in chunks of 32,
+// staged in shared memory as float-float; thread (row = tid % 32, col = tid / 32 + 8 q)
+// accumulates over the bases in order: deterministic, FP64-grade on the FP32 pipes.
+// ---------------------------------------------------------------------------------------------
+struct ReconParams {
+    const double* Y;
+    int64_t m, d, ldy;
+    const double* T;
+    int64_t n, ldt;
+    double* Xr;
+    int64_t ldxr;
+};
+
+__global__ void __launch_bounds__(256) reconstruct_kernel(ReconParams p) {
+    __shared__ float yh[kPT][kPT], yl[kPT][kPT];           // [basis][row]
+    __shared__ float th[kPT][kPT + 1], tl[kPT][kPT + 1];   // [col][basis]
+    const int tid = threadIdx.x;
+    const int row = tid % kPT, cq = tid / kPT;
+    const int64_t r0 = (int64_t)blockIdx.x * kPT, j0 = (int64_t)blockIdx.y * kPT;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t l0 = 0; l0 < p.d; l0 += kPT) {
+        for (int idx = tid; idx < kPT * kPT; idx += 256) {
+            const int a = idx % kPT, b = idx / kPT;
+            // Y(r0 + a, l0 + b) and T(l0 + a, j0 + b)
+            double y = 0.0, t = 0.0;
+            if (r0 + a < p.m && l0 + b < p.d) y = p.Y[(l0 + b) * p.ldy + r0 + a];
+            if (l0 + a < p.d && j0 + b < p.n) t = p.T[(j0 + b) * p.ldt + l0 + a];
+            float hi, lo;
+            split_double(y, hi, lo);
+            yh[b][a] = hi;
+            yl[b][a] = lo;
+            split_double(t, hi, lo);
+            th[b][a] = hi;
+            tl[b][a] = lo;
+        }
+        __syncthreads();
+        const int lc = (int)min((int64_t)kPT, p.d - l0);
+        for (int l = 0; l < lc; ++l) {
+            const float ah = yh[l][row], al = yl[l][row];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ff_mac2(s[q], c[q], ah, al, th[cq + 8 * q][l], tl[cq + 8 * q][l]);
+        }
+        __syncthreads();
+    }
+    if (r0 + row < p.m) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t j = j0 + cq + 8 * q;
+            if (j < p.n) p.Xr[j * p.ldxr + r0 + row] = ff_to_double(s[q], c[q]);
+        }
+    }
+}
+
+cudaError_t launch_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy, const double* T, int64_t n,
+                               int64_t ldt, double* Xr, int64_t ldxr, cudaStream_t st) {
+    ReconParams p{Y, m, d, ldy, T, n, ldt, Xr, ldxr};
+    dim3 grid((unsigned)ceil_div(m, (int64_t)kPT), (unsigned)ceil_div(n, (int64_t)kPT));
+    reconstruct_kernel<<<grid, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace rbd

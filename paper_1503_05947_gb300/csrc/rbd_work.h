@@ -176,6 +176,8 @@ cudaError_t launch_pass(const Work& w, double* Y, int64_t ldy, double* T, int64_
                         uint32_t* progress, cudaStream_t st);
 cudaError_t launch_project(const double* Y, int64_t m, int64_t d, int64_t ldy, const void* V, int vt,
                            int64_t k, int64_t ldv, double* C, int64_t ldc, cudaStream_t st);
+cudaError_t launch_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy, const double* T, int64_t n,
+                               int64_t ldt, double* Xr, int64_t ldxr, cudaStream_t st);
 // Dynamic shared-memory opt-in for the pass kernels and their resident CTAs per SM, indexed by
 // storage type (once per device).
 cudaError_t pass_kernel_setup(int ctas_per_sm[3]);

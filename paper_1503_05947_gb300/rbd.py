@@ -101,6 +101,8 @@ def load():
     lib.rbd_batch_plan_destroy.argtypes = [_PTR]
     lib.rbd_compress_batched.restype = ctypes.c_int
     lib.rbd_compress_batched.argtypes = [ctypes.POINTER(_Instance), _I64, ctypes.c_int, _PTR, _PTR]
+    lib.rbd_reconstruct.restype = ctypes.c_int
+    lib.rbd_reconstruct.argtypes = [_PTR, _I64, _I64, _I64, _PTR, _I64, _I64, _PTR, _I64, _PTR]
     lib.rbd_project.restype = ctypes.c_int
     lib.rbd_project.argtypes = [_PTR, _I64, _I64, _I64, _PTR, ctypes.c_int, _I64, _I64, _PTR, _I64, _PTR]
     lib.rbd_set_profiling.restype = None
@@ -302,6 +304,28 @@ def grad(X: torch.Tensor, Y: torch.Tensor, T: torch.Tensor, pivots: torch.Tensor
                           loss.data_ptr(), _stream_ptr(dev))
     _check(st, "rbd_grad")
     return G, loss
+
+
+def reconstruct(Y: torch.Tensor, T: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Uncompress (Section 3.1): Xr = Y T for column-major FP64 CUDA tensors Y (m x d) and T (d x n),
+    or Y c for a vector c."""
+    lib = load()
+    if Y.dtype != torch.float64 or T.dtype != torch.float64 or not Y.is_cuda or not T.is_cuda:
+        raise ValueError("Y and T must be CUDA float64 tensors")
+    if T.dim() == 1:
+        T = T[:, None]
+    m, d = Y.shape
+    if T.shape[0] != d:
+        raise ValueError("T must have d rows")
+    n = T.shape[1]
+    ldy = _colmajor(Y, "Y") if d > 0 else m
+    ldt = _colmajor(T, "T") if d > 0 else 1
+    Xr = colmajor_empty(m, n, torch.float64, Y.device) if out is None else out
+    with torch.cuda.device(Y.device):
+        st = lib.rbd_reconstruct(Y.data_ptr() if d > 0 else None, m, d, ldy, T.data_ptr() if d > 0 else None, n,
+                                 ldt, Xr.data_ptr(), _colmajor(Xr, "out"), _stream_ptr(Y.device))
+    _check(st, "rbd_reconstruct")
+    return Xr
 
 
 def project(Y: torch.Tensor, V: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
