@@ -198,6 +198,19 @@ def pin_paper_approx_example(compress):
     assert pw < g["pointwise_error_below"], f"pointwise error {pw:.3e}"
     m, n = X.shape
     assert m * n / ((m + n) * r["d"]) > g["compression_ratio_above"]
+    # RBD matches SVD: e_S(d) <= e_R(d) (Eckart-Young) and e_R(d) within a small factor of e_S(d)
+    from scipy.sparse.linalg import svds
+    cmp_ = g["svd_comparison"]
+    u, s, vt = svds(X, k=cmp_["d_range"][1] + 2)
+    o = np.argsort(s)[::-1]
+    u, s, vt = u[:, o], s[o], vt[o]
+    xf = float(np.linalg.norm(X))
+    for d in range(cmp_["d_range"][0], cmp_["d_range"][1] + 1):
+        e_r = np.linalg.norm(X - r["Y"][:, :d] @ r["T"][:d])
+        e_s = np.linalg.norm(X - (u[:, :d] * s[:d]) @ vt[:d])
+        assert e_r >= e_s * (1 - 1e-6) - 1e-12 * xf, f"d={d}: below the SVD error"
+        assert e_r <= cmp_["frobenius_ratio_at_most"] * e_s + 1e-12 * xf, f"d={d}: {e_r:.3e} vs SVD {e_s:.3e}"
+    del u, vt
 
 
 def pin_eckart_young(compress):
