@@ -135,6 +135,29 @@ rbd_status rbd_compress(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64
                         void* stream, rbd_result* result);
 
 /*
+ * rbd_compress_resume -- continue a compression to a larger d_max: Algorithm 1's loop picks up
+ * after d0 bases from its outputs (a checkpoint of the greedy state).
+ *
+ *  X, xt, m, n, ldx, tol, mode, workspace, stream, result  as for rbd_compress (the same X,
+ *                tolerance and mode as the call being continued).
+ *  d0          [in]  1 <= d0 <= d_max: bases already in Y, T, pivots (and err, nu).
+ *  next_pivot  [in]  the column the next basis uses (rbd_result.next_pivot of that call).
+ *  d_max       [in]  the new limit; Y, T, pivots, err, nu must have capacity d_max, and hold the
+ *                    first d0 columns / rows / entries.
+ *  The running indicator e_j, the Frobenius residual and the split copy of Y are rebuilt from
+ *  Y(:, 0:d0), T(0:d0, :) and pivots with the operations and order the loop used, so the
+ *  continued run gives the results of one rbd_compress call with this d_max (the same bits, on
+ *  the same path).  err[d0 - 1] is rewritten (certified again); entries from d0 on are new.
+ *  Errors: those of rbd_compress, and RBD_EINVAL for d0 or next_pivot out of range.
+ */
+rbd_status rbd_compress_resume(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
+                               double tol, rbd_tol_mode mode, int64_t d0, int64_t next_pivot,
+                               int64_t d_max, double* Y, int64_t ldy, double* T, int64_t ldt,
+                               int64_t* pivots, double* err, double* nu,
+                               void* workspace, size_t workspace_bytes,
+                               void* stream, rbd_result* result);
+
+/*
  * rbd_compress_host -- rbd_compress on HOST buffers (end-to-end form).
  *
  * Same arguments and layout as rbd_compress, but X, Y, T, pivots, err and nu (nu may be

@@ -12,6 +12,7 @@ from .rbd import (  # noqa: F401
     compress,
     compress_host,
     compress_noalloc,
+    compress_resume,
     grad,
     get_profile,
     load,

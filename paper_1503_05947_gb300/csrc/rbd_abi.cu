@@ -288,11 +288,13 @@ static bool valid_dtype(int t) { return t == RBD_F64 || t == RBD_F32 || t == RBD
 // ---------------------------------------------------------------------------------------
 // The greedy loop on device buffers
 // ---------------------------------------------------------------------------------------
+// k0 > 0 continues a compression after k0 bases (Y, T, pivots hold them; next_pivot is the
+// column the next basis uses); k0 = 0 starts from `start`.
 static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol,
                                   rbd_tol_mode mode, int64_t d_max, int64_t start, double* Y, int64_t ldy,
                                   double* T, int64_t ldt, int64_t* pivots, double* err, double* nu,
                                   void* workspace, size_t workspace_bytes, cudaStream_t st,
-                                  rbd_result* result) {
+                                  rbd_result* result, int64_t k0 = 0, int64_t next_pivot = 0) {
     DeviceState ds;
     cudaError_t ce = device_state(ds);
     if (ce != cudaSuccess) return map_cuda(ce);
@@ -345,6 +347,10 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
         ce = launch_init(w, X, tol, (int)mode, start, st);
         ++launches;
     }
+    if (ce == cudaSuccess && k0 > 0) {
+        ce = launch_resume(w, Y, ldy, T, ldt, pivots, k0, next_pivot, st);
+        launches += 3;
+    }
     if (ce == cudaSuccess && prof) cudaEventRecord(ev_init1, st);
 
     cudaEvent_t ev_loop0 = nullptr, ev_loop1 = nullptr;
@@ -355,13 +361,14 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
             ev_loop1 = new_event();
             cudaEventRecord(ev_loop0, st);
         }
-        ce = launch_loop(w, X, Y, ldy, T, ldt, pivots, err, nu, st);
+        ce = launch_loop(w, X, Y, ldy, T, ldt, pivots, err, nu, k0, st);
         ++launches;
         if (prof) cudaEventRecord(ev_loop1, st);
     }
     // stepwise path: orthogonalisation steps k = 0..d_max (the last one only certifies E_cur of
     // basis d_max - 1 and takes the final stop decision); passes k = 0..d_max-1
-    for (int64_t k = 0; !w.use_loop && k <= d_max && ce == cudaSuccess; ++k) {
+    if (prog_h) prog_h[0] = (uint32_t)k0;
+    for (int64_t k = k0; !w.use_loop && k <= d_max && ce == cudaSuccess; ++k) {
         if (prog_h && k >= kLookahead) {
             // stay at most kLookahead steps ahead of the device; stop launching once it stopped
             volatile uint32_t* pr = prog_h;
@@ -527,6 +534,17 @@ rbd_status rbd_compress(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64
     if (v != RBD_OK) return v;
     return compress_device(X, xt, m, n, ldx, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err, nu,
                            workspace, workspace_bytes, (cudaStream_t)stream, result);
+}
+
+rbd_status rbd_compress_resume(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol,
+                               rbd_tol_mode mode, int64_t d0, int64_t next_pivot, int64_t d_max, double* Y,
+                               int64_t ldy, double* T, int64_t ldt, int64_t* pivots, double* err, double* nu,
+                               void* workspace, size_t workspace_bytes, void* stream, rbd_result* result) {
+    rbd_status v = validate(X, xt, m, n, ldx, tol, mode, d_max, 0, Y, ldy, T, ldt, pivots, err);
+    if (v != RBD_OK) return v;
+    if (d0 < 1 || d0 > d_max || next_pivot < 0 || next_pivot >= n) return RBD_EINVAL;
+    return compress_device(X, xt, m, n, ldx, tol, mode, d_max, next_pivot, Y, ldy, T, ldt, pivots, err, nu,
+                           workspace, workspace_bytes, (cudaStream_t)stream, result, d0, next_pivot);
 }
 
 rbd_status rbd_compress_host(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol,

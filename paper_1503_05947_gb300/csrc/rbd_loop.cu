@@ -38,6 +38,7 @@ constexpr uint64_t kBarrierLimitNs = 2000000000ull;
 
 struct LoopParams {
     int64_t m, n, ldp, ldx, ldt, ldy, d_max;
+    int64_t k0;           // first basis index of this launch (0, or d0 when resuming)
     int xt;
     // X planes (tile-major) and pass geometry
     const unsigned char* planes;
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     const uint64_t pol_x = p.evict_first ? l2_policy_evict_first() : l2_policy_evict_normal();
     const uint64_t pol_xi = l2_policy_evict_normal();
 
-    int64_t k = 0;
+    int64_t k = p.k0;
     int32_t stop = STOP_NONE;
     double nu = 0.0;
     for (;; ++k) {
@@ -836,8 +837,9 @@ cudaError_t loop_kernel_setup(int max_smem) {
 }
 
 cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, double* T, int64_t ldt,
-                        int64_t* pivots, double* err, double* nu_out, cudaStream_t st) {
+                        int64_t* pivots, double* err, double* nu_out, int64_t k0, cudaStream_t st) {
     LoopParams p;
+    p.k0 = k0;
     p.m = w.m;
     p.n = w.n;
     p.ldp = w.ldp;

@@ -136,7 +136,7 @@ extern "C" rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t 
     }
     if (w.use_loop) {
         if (ce == cudaSuccess) {
-            ce = launch_loop(w, X, Y, ldy, T, ldt, pivots, err, nu, st);
+            ce = launch_loop(w, X, Y, ldy, T, ldt, pivots, err, nu, 0, st);
             ++launches;
         }
     } else {

@@ -176,6 +176,10 @@ cudaError_t launch_pass(const Work& w, double* Y, int64_t ldy, double* T, int64_
                         uint32_t* progress, cudaStream_t st);
 cudaError_t launch_project(const double* Y, int64_t m, int64_t d, int64_t ldy, const void* V, int vt,
                            int64_t k, int64_t ldv, double* C, int64_t ldc, cudaStream_t st);
+// Restore the loop state after k0 bases (rbd_compress_resume): e_j, the group sums, the split
+// copy of Y for the path in use, and fro_last / pivot / d in the control block.
+cudaError_t launch_resume(const Work& w, const double* Y, int64_t ldy, const double* T, int64_t ldt,
+                          const int64_t* pivots, int64_t k0, int64_t next_pivot, cudaStream_t st);
 cudaError_t launch_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy, const double* T, int64_t n,
                                int64_t ldt, double* Xr, int64_t ldxr, cudaStream_t st);
 // Dynamic shared-memory opt-in for the pass kernels and their resident CTAs per SM, indexed by
@@ -188,6 +192,6 @@ size_t loop_smem_bytes(int xt, int R, int LC);
 int loop_chunk_cols_for(int xt, int R);
 cudaError_t loop_kernel_setup(int max_smem);
 cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, double* T, int64_t ldt,
-                        int64_t* pivots, double* err, double* nu_out, cudaStream_t st);
+                        int64_t* pivots, double* err, double* nu_out, int64_t k0, cudaStream_t st);
 
 }  // namespace rbd

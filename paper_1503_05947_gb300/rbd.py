@@ -82,6 +82,10 @@ def load():
     lib.rbd_compress_host.restype = ctypes.c_int
     lib.rbd_compress_host.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
                                       _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.POINTER(_Result)]
+    lib.rbd_compress_resume.restype = ctypes.c_int
+    lib.rbd_compress_resume.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64, _I64,
+                                        _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.c_size_t, _PTR,
+                                        ctypes.POINTER(_Result)]
     lib.rbd_compress_noalloc.restype = ctypes.c_int
     lib.rbd_compress_noalloc.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
                                          _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.POINTER(_Result)]
@@ -200,6 +204,45 @@ def compress(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: 
                               err.data_ptr(), nu.data_ptr(), ws_ptr, ws_bytes, _stream_ptr(dev),
                               ctypes.byref(res))
     _check(st, "rbd_compress")
+    d = int(res.d)
+    return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
+                      STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),
+                      float(res.x_fro), float(res.x_maxcol), int(res.launches))
+
+
+def compress_resume(X: torch.Tensor, prev: Compressed, tol: float, d_max: int, tol_mode: str = "maxcol_abs",
+                    workspace: Optional[torch.Tensor] = None) -> Compressed:
+    """rbd_compress_resume: continue the compression ``prev`` of X (same X, tolerance and mode) to
+    a larger d_max; the result equals one compress call with that d_max."""
+    lib = load()
+    if not X.is_cuda or X.dtype not in DTYPES:
+        raise ValueError("X must be a CUDA tensor of a supported dtype")
+    m, n = X.shape
+    ldx = _colmajor(X, "X")
+    d0 = prev.d
+    if d0 < 1 or d_max < d0:
+        raise ValueError("need 1 <= prev.d <= d_max")
+    dev = X.device
+    Y = colmajor_empty(m, d_max, torch.float64, dev)
+    T = colmajor_empty(d_max, n, torch.float64, dev)
+    piv = torch.empty(d_max, dtype=torch.int64, device=dev)
+    err = torch.empty(d_max, dtype=torch.float64, device=dev)
+    nu = torch.empty(d_max, dtype=torch.float64, device=dev)
+    Y[:, :d0].copy_(prev.Y)
+    T[:d0, :].copy_(prev.T)
+    piv[:d0].copy_(prev.pivots)
+    err[:d0].copy_(prev.err)
+    nu[:d0].copy_(prev.nu)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    res = _Result()
+    with torch.cuda.device(dev):
+        st = lib.rbd_compress_resume(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, float(tol), TOL_MODES[tol_mode], d0,
+                                     int(prev.next_pivot), int(d_max), Y.data_ptr(), m, T.data_ptr(), d_max,
+                                     piv.data_ptr(), err.data_ptr(), nu.data_ptr(), ws_ptr, ws_bytes,
+                                     _stream_ptr(dev), ctypes.byref(res))
+    _check(st, "rbd_compress_resume")
     d = int(res.d)
     return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
                       STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),
