@@ -17,6 +17,7 @@ from .inputs import (  # noqa: F401
     paper_rank_function,
     paper_approx_function,
     orthogonal_columns,
+    row_weights,
     out_of_sample,
     batch_specs,
     decay_spectrum,

@@ -199,6 +199,19 @@ def orthogonal_columns(m: int, norms, seed: int = 0) -> np.ndarray:
     return x
 
 
+def row_weights(m: int, seed: int = 0, lo: float = 0.1, hi: float = 10.0) -> np.ndarray:
+    """m positive weights for the diagonal A-norm of Section 3.2: a smooth profile (a Gaussian
+    bump over a random third of the rows, "part of each entry preserved better") times a seeded
+    log-uniform factor per row, clipped to [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    r = np.arange(m, dtype=np.float64)
+    c = rng.uniform(0.2, 0.8) * m
+    width = max(m / 6.0, 1.0)
+    smooth = 1.0 + (hi - 1.0) * np.exp(-0.5 * ((r - c) / width) ** 2)
+    jitter = np.exp(rng.uniform(np.log(0.5), np.log(2.0), m))
+    return np.clip(smooth * jitter, lo, hi)
+
+
 def out_of_sample(m: int, k: int, seed: int) -> np.ndarray:
     """k i.i.d. N(0, 1/m) vectors of length m, column-major m x k."""
     rng = np.random.default_rng(seed)

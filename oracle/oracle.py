@@ -53,6 +53,9 @@ def load(mutant: int = 0):
         lib.rbd_oracle_compress.restype = ctypes.c_int
         lib.rbd_oracle_compress.argtypes = [ptr, i64, i64, i64, dbl, ctypes.c_int, i64, i64, dbl,
                                             ptr, i64, ptr, i64, ptr, ptr, ptr, ptr, ptr, ptr]
+        lib.rbd_oracle_compress_weighted.restype = ctypes.c_int
+        lib.rbd_oracle_compress_weighted.argtypes = [ptr, i64, i64, i64, ptr, dbl, ctypes.c_int, i64, i64, dbl,
+                                                     ptr, i64, ptr, i64, ptr, ptr, ptr, ptr, ptr, ptr]
         lib.rbd_oracle_project.restype = ctypes.c_int
         lib.rbd_oracle_project.argtypes = [ptr, i64, i64, i64, ptr, i64, i64, ptr, i64]
         lib.rbd_oracle_grad.restype = ctypes.c_int
@@ -76,12 +79,18 @@ def _p(a: np.ndarray):
 
 
 def compress(X, tol: float, d_max: int, start: int = 0, mode: str = "maxcol_abs",
-             rank_floor: float = RANK_FLOOR, mutant: int = 0) -> dict:
+             rank_floor: float = RANK_FLOOR, mutant: int = 0, weights=None) -> dict:
     """Run Algorithm 1 on column-major FP64 X (m x n).  Returns a dict with Y (m x d),
-    T (d x n), pivots, err, nu, fro (length d), next_pivot and d."""
+    T (d x n), pivots, err, nu, fro (length d), next_pivot and d.  With `weights` (m positive
+    values, A = diag(weights)) the error of steps 2.2-2.4 is the A-norm (Section 3.2)."""
     lib = load(mutant)
     X = _f64_colmajor(X)
     m, n = X.shape
+    w = None
+    if weights is not None:
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+        if w.size != m:
+            raise ValueError("weights must have one entry per row of X")
     Y = np.zeros((m, d_max), dtype=np.float64, order="F")
     T = np.zeros((d_max, n), dtype=np.float64, order="F")
     piv = np.zeros(d_max, dtype=np.int64)
@@ -90,9 +99,14 @@ def compress(X, tol: float, d_max: int, start: int = 0, mode: str = "maxcol_abs"
     fro = np.zeros(d_max)
     nxt = np.zeros(1, dtype=np.int64)
     dout = np.zeros(1, dtype=np.int64)
-    rc = lib.rbd_oracle_compress(_p(X), m, n, m, float(tol), TOL_MODES[mode], int(d_max), int(start),
-                                 float(rank_floor), _p(Y), m, _p(T), d_max, _p(piv), _p(err), _p(nu),
-                                 _p(fro), _p(nxt), _p(dout))
+    if w is None:
+        rc = lib.rbd_oracle_compress(_p(X), m, n, m, float(tol), TOL_MODES[mode], int(d_max), int(start),
+                                     float(rank_floor), _p(Y), m, _p(T), d_max, _p(piv), _p(err), _p(nu),
+                                     _p(fro), _p(nxt), _p(dout))
+    else:
+        rc = lib.rbd_oracle_compress_weighted(_p(X), m, n, m, _p(w), float(tol), TOL_MODES[mode], int(d_max),
+                                              int(start), float(rank_floor), _p(Y), m, _p(T), d_max, _p(piv),
+                                              _p(err), _p(nu), _p(fro), _p(nxt), _p(dout))
     if rc != 0:
         raise ValueError(f"rbd_oracle_compress failed with status {rc}")
     d = int(dout[0])

@@ -17,6 +17,13 @@
  *   - Section 3.2, Eq. (evalerr) with A = I: the error of column j is its Euclidean residual.
  *     The oracle evaluates it from the DEFINITION, as the norm of the explicit residual
  *     R(:, j) = X(:, j) - sum_{l <= d} xi_l T(l, j), the terms summed in the order l = 1..d.
+ *   - Section 3.2 with a general DIAGONAL A = diag(w), w_r > 0 (rbd_oracle_compress_weighted):
+ *     the basis stays the Euclidean Gram-Schmidt basis of Algorithm 1 and T = Y' X, and only the
+ *     error of step 2.3 is measured in the A-norm, ||v||_A = sqrt(sum_r w_r v_r^2) (Eq. (evalerr)
+ *     with c = T(:, j) = Y' v; the paper pre-computes Y'AX and Y'AY for it, which an
+ *     A-orthonormal basis would not need).  The oracle evaluates ||R(:, j)||_A of the explicit
+ *     residual; step 2.2's break test and step 2.4's E_cur use the same A-norm, the
+ *     normalisation xi_d = v / ||v|| and the rank floor stay Euclidean.
  *   - Section 3.1, "Evaluate the compression of out-of-sample data": v_C = Y' v.
  *   - Section 3.1, "Uncompress": X(:, j) ~ Y T(:, j).
  *
@@ -41,7 +48,9 @@
  * definition of the indicator recomputed from scratch, Householder QR of the pivot columns,
  * brute-force least-squares pivots on tiny inputs, closed forms on orthogonal columns, exact
  * recovery of the paper's rank-1/2/3 functions (Section 4.2.1), the paper's pointwise error
- * bound for its 5001 x 5001 example (Section 4.2.2) and the Eckart-Young bound.  Planted
+ * bound for its 5001 x 5001 example (Section 4.2.2) and the Eckart-Young bound; the diagonal
+ * A-norm form against the A-norm indicator recomputed from scratch, least-squares brute force
+ * in the A-norm, closed forms on coordinate-aligned columns, termination and scaling.  Planted
  * mistakes (RBD_ORACLE_MUTANT) must each fail at least one of those pins.
  */
 #include <math.h>
@@ -71,6 +80,14 @@ static double dot(const double* a, const double* b, int64_t m) {
 
 static double norm2(const double* a, int64_t m) { return sqrt(dot(a, a, m)); }
 
+/* ||a||_A = sqrt(sum_r w[r] a[r]^2) for A = diag(w), left to right; w == NULL is A = I. */
+static double norm_a(const double* a, const double* w, int64_t m) {
+    if (!w) return norm2(a, m);
+    double s = 0.0;
+    for (int64_t r = 0; r < m; ++r) s += w[r] * (a[r] * a[r]);
+    return sqrt(s);
+}
+
 int rbd_oracle_version(void) { return 1; }
 
 /*
@@ -85,10 +102,10 @@ int rbd_oracle_version(void) { return 1; }
  *   next_pivot       = the argmax of the last step 2.3 (the column the next basis would use)
  *   d_out            = number of bases produced
  */
-int rbd_oracle_compress(const double* X, int64_t m, int64_t n, int64_t ldx, double tol, int mode,
-                        int64_t d_max, int64_t start, double rank_floor, double* Y, int64_t ldy,
-                        double* T, int64_t ldt, int64_t* pivots, double* err, double* nu,
-                        double* fro, int64_t* next_pivot, int64_t* d_out) {
+static int compress_core(const double* X, int64_t m, int64_t n, int64_t ldx, const double* w, double tol,
+                         int mode, int64_t d_max, int64_t start, double rank_floor, double* Y, int64_t ldy,
+                         double* T, int64_t ldt, int64_t* pivots, double* err, double* nu, double* fro,
+                         int64_t* next_pivot, int64_t* d_out) {
     if (!X || !Y || !T || !pivots || !err || !nu || !fro || !next_pivot || !d_out) return ORC_EINVAL;
     if (m < 1 || n < 1 || ldx < m || ldy < m || d_max < 1 || ldt < d_max) return ORC_EINVAL;
     if (d_max > m || d_max > n) return ORC_EINVAL;
@@ -118,7 +135,7 @@ int rbd_oracle_compress(const double* X, int64_t m, int64_t n, int64_t ldx, doub
             }
             R[j * m + r] = xj[r];
         }
-        double nj = norm2(xj, m);
+        double nj = norm_a(xj, w, m);
         if (nj > maxcol) maxcol = nj;
         fro2x += nj * nj;
     }
@@ -145,7 +162,8 @@ int rbd_oracle_compress(const double* X, int64_t m, int64_t n, int64_t ldx, doub
             }
         }
         double vn = norm2(v, m);
-        if (vn < eps_r || vn <= rank_floor * xin) break;
+        double vna = (RBD_ORACLE_MUTANT == 15) ? vn : norm_a(v, w, m);
+        if (vna < eps_r || vn <= rank_floor * xin) break;
         double* xi = Y + d * ldy;
         for (int64_t r = 0; r < m; ++r) xi[r] = (RBD_ORACLE_MUTANT == 6) ? v[r] : v[r] / vn;
         /* T(d, :) = xi_d' X */
@@ -158,7 +176,7 @@ int rbd_oracle_compress(const double* X, int64_t m, int64_t n, int64_t ldx, doub
             double c = T[j * ldt + d];
             double* rj = R + j * m;
             for (int64_t r = 0; r < m; ++r) rj[r] -= c * xi[r];
-            double ej = norm2(rj, m);
+            double ej = (RBD_ORACLE_MUTANT == 14) ? norm2(rj, m) : norm_a(rj, w, m);
             if (RBD_ORACLE_MUTANT == 5) ej = ej * ej;
             fro2 += ej * ej;
             int better = (RBD_ORACLE_MUTANT == 3) ? (ej >= ecur) : (ej > ecur);
@@ -186,6 +204,32 @@ int rbd_oracle_compress(const double* X, int64_t m, int64_t n, int64_t ldx, doub
     free(R);
     free(v);
     return ORC_OK;
+}
+
+int rbd_oracle_compress(const double* X, int64_t m, int64_t n, int64_t ldx, double tol, int mode,
+                        int64_t d_max, int64_t start, double rank_floor, double* Y, int64_t ldy,
+                        double* T, int64_t ldt, int64_t* pivots, double* err, double* nu,
+                        double* fro, int64_t* next_pivot, int64_t* d_out) {
+    return compress_core(X, m, n, ldx, NULL, tol, mode, d_max, start, rank_floor, Y, ldy, T, ldt, pivots, err,
+                         nu, fro, next_pivot, d_out);
+}
+
+/*
+ * Algorithm 1 with the error of steps 2.2-2.4 in the A-norm of A = diag(w) (Section 3.2, "general
+ * diagonal matrix"): w holds m weights, each finite and > 0.  Outputs as rbd_oracle_compress, with
+ * err[k] = max_j ||X(:, j) - Y(:, 0:k) T(0:k, j)||_A and fro[k] = sqrt(sum_j ||.||_A^2); nu[k] stays
+ * the Euclidean ||v|| that normalises xi_k.  The relative tolerance modes scale by max_j ||x_j||_A and
+ * sqrt(sum_j ||x_j||_A^2).
+ */
+int rbd_oracle_compress_weighted(const double* X, int64_t m, int64_t n, int64_t ldx, const double* w, double tol,
+                                 int mode, int64_t d_max, int64_t start, double rank_floor, double* Y, int64_t ldy,
+                                 double* T, int64_t ldt, int64_t* pivots, double* err, double* nu, double* fro,
+                                 int64_t* next_pivot, int64_t* d_out) {
+    if (!w || m < 1) return ORC_EINVAL;
+    for (int64_t r = 0; r < m; ++r)
+        if (!isfinite(w[r]) || !(w[r] > 0.0)) return ORC_EINVAL;
+    return compress_core(X, m, n, ldx, w, tol, mode, d_max, start, rank_floor, Y, ldy, T, ldt, pivots, err, nu,
+                         fro, next_pivot, d_out);
 }
 
 /* Out-of-sample map (Section 3.1): C(:, k) = Y' V(:, k) for k < nv; C is d x nv (ldc). */

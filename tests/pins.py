@@ -259,6 +259,132 @@ def pin_zero_matrix(compress):
     assert compress(X, 0.0, 3)["d"] == 0
 
 
+# ---------------------------------------------------------------------------------------------
+# Diagonal A-norm (Section 3.2, "general diagonal matrix"): compress(..., weights=w) keeps the
+# Euclidean Gram-Schmidt basis and T = Y' X and measures the error of steps 2.2-2.4 in
+# ||v||_A = sqrt(sum_r w_r v_r^2).
+# ---------------------------------------------------------------------------------------------
+def _anorm(R, w):
+    return np.sqrt((w[:, None] * R * R).sum(axis=0))
+
+
+def pin_w_indicator_definition(compress):
+    """With weights: err[k] = max_j ||X(:, j) - Y(:, 0:k) T(0:k, j)||_A from scratch, its argmax
+    is the next pivot, Y'Y = I and T = Y' X (the basis stays Euclidean)."""
+    X = _decay(150, 110, 21, rate=0.2, noise=1e-7)
+    w = gen.row_weights(150, seed=1)
+    r = compress(X, 0.0, 28, weights=w)
+    d = r["d"]
+    assert d == 28, f"expected 28 bases, got {d}"
+    Y = r["Y"]
+    assert np.abs(Y.T @ Y - np.eye(d)).max() <= 10 * d * EPS, "Y'Y != I"
+    scale = np.linalg.norm(X, axis=0)
+    assert (np.abs(r["T"] - Y.T @ X) / scale[None, :]).max() <= 1e-13, "T != Y'X"
+    sa = _anorm(X, w).max()
+    for k in range(d):
+        cn = _anorm(X - Y[:, :k + 1] @ r["T"][:k + 1, :], w)
+        assert abs(r["err"][k] - cn.max()) <= 1e-12 * sa, f"err[{k}] {r['err'][k]} vs {cn.max()}"
+        srt = np.sort(cn)
+        if k + 1 < d and srt[-1] - srt[-2] > 1e-9 * sa:
+            assert r["pivots"][k + 1] == int(np.argmax(cn)), f"pivot {k + 1}"
+
+
+def pin_w_bruteforce_tiny(compress):
+    """Tiny inputs with weights: the next pivot maximises ||x_j - X(:, P) c||_A over j, c the
+    Euclidean least-squares coefficients (T = Y' X), independent of Gram-Schmidt and the update."""
+    rng = np.random.default_rng(25)
+    checked = 0
+    for trial in range(40):
+        m = int(rng.integers(2, 9))
+        n = int(rng.integers(2, 9))
+        X = np.asfortranarray(rng.standard_normal((m, n)))
+        w = np.exp(rng.uniform(np.log(0.05), np.log(20.0), m))
+        start = int(rng.integers(0, n))
+        r = compress(X, 0.0, min(m, n), start=start, weights=w)
+        assert r["pivots"][0] == start
+        sa = _anorm(X, w).max()
+        for k in range(r["d"]):
+            A = X[:, r["pivots"][:k + 1]]
+            res = np.empty(n)
+            for j in range(n):
+                c, *_ = np.linalg.lstsq(A, X[:, j], rcond=None)
+                res[j] = np.sqrt((w * (X[:, j] - A @ c) ** 2).sum())
+            assert abs(r["err"][k] - res.max()) <= 1e-11 * sa, f"trial {trial} step {k}"
+            srt = np.sort(res)
+            if k + 1 < r["d"] and n > 1 and srt[-1] - srt[-2] > 1e-8 * sa:
+                assert r["pivots"][k + 1] == int(np.argmax(res)), f"trial {trial} pivot {k + 1}"
+                checked += 1
+    assert checked > 20
+
+
+def pin_w_closed_form_orthogonal(compress):
+    """Columns norms[j] e_p(j): no column has a component along another, so each residual is the
+    column itself and the pivots follow decreasing ||x_j||_A = norms[j] sqrt(w[p(j)]) (an order the
+    weights make different from the Euclidean one); err[k] is the largest A-norm not yet chosen
+    and nu[k] the chosen column's Euclidean norm."""
+    norms = np.array([3.0, 7.0, 1.0, 5.0, 2.0, 6.0, 4.0])
+    X = gen.orthogonal_columns(12, norms, seed=3)
+    rows = np.argmax(np.abs(X), axis=0)
+    w = np.full(12, 1.0)
+    w[rows] = np.array([16.0, 0.25, 30.0, 1.0, 9.0, 0.5, 2.0])
+    an = norms * np.sqrt(w[rows])
+    assert len(set(np.round(an, 9))) == 7 and list(np.argsort(-an)) != list(np.argsort(-norms))
+    start = 2
+    r = compress(X, 0.0, 7, start=start, weights=w)
+    order = [start] + [int(j) for j in np.argsort(-an) if j != start]
+    assert list(r["pivots"]) == order, f"pivots {list(r['pivots'])} != {order}"
+    for k in range(r["d"]):
+        remaining = [an[j] for j in range(7) if j not in order[:k + 1]]
+        expect = max(remaining) if remaining else 0.0
+        assert abs(r["err"][k] - expect) <= 1e-14 * an.max(), f"err[{k}] {r['err'][k]} != {expect}"
+        assert abs(r["nu"][k] - norms[order[k]]) <= 1e-14 * norms.max(), f"nu[{k}]"
+
+
+def pin_w_termination(compress):
+    """Steps 2.2 and 2.4 compare the A-norm with eps_R; the relative modes scale by the A-norms
+    of X."""
+    norms = np.array([8.0, 4.0, 2.0, 1.0])
+    X = gen.orthogonal_columns(6, norms, seed=9)
+    rows = np.argmax(np.abs(X), axis=0)
+    w = np.full(6, 1.0)
+    w[rows] = np.array([0.25, 6.25, 1.0, 9.0])   # A-norms 4, 10, 2, 3
+    r = compress(X, 0.0, 4, start=1, weights=w)
+    assert r["pivots"].tolist() == [1, 0, 3, 2]
+    assert np.abs(r["err"] - np.array([4.0, 3.0, 2.0, 0.0])).max() <= 1e-14 * 10
+    assert compress(X, 4.0, 4, start=1, weights=w)["d"] == 1     # E_1 = 4 <= 4
+    assert compress(X, 3.99, 4, start=1, weights=w)["d"] == 2    # E_2 = 3 <= 3.99
+    assert compress(X, 2.5, 4, start=1, weights=w)["d"] == 3     # E_3 = 2 <= 2.5
+    # eps_R = 0.35 max_j ||x_j||_A = 3.5 (the Euclidean maximum would give 2.8 and d = 3)
+    assert compress(X, 0.35, 4, start=1, mode="maxcol_rel", weights=w)["d"] == 2
+    # step 2.2 on the start column: ||x_0||_A = 4 < 5 <= ||x_0|| = 8
+    assert compress(X, 5.0, 4, start=0, weights=w)["d"] == 0
+    # Frobenius in the A-norm: ||X||_F,A = sqrt(129) = 11.36; after one basis sqrt(29) = 5.39,
+    # after two sqrt(13) = 3.61
+    assert compress(X, 0.48, 4, start=1, mode="fro_rel", weights=w)["d"] == 1
+    assert compress(X, 0.47, 4, start=1, mode="fro_rel", weights=w)["d"] == 2
+
+
+def pin_w_scaling(compress):
+    """A = alpha diag(w): the same bases and pivots, errors times sqrt(alpha); A = I (all weights
+    one) gives the unweighted result."""
+    X = _decay(120, 90, 23, rate=0.25, noise=1e-7)
+    w = gen.row_weights(120, seed=2)
+    r1 = compress(X, 0.0, 20, weights=w)
+    r4 = compress(X, 0.0, 20, weights=4.0 * w)
+    assert list(r1["pivots"]) == list(r4["pivots"])
+    assert np.abs(r1["Y"] - r4["Y"]).max() <= 1e-13
+    sa = r1["err"].max()
+    assert np.abs(r4["err"] - 2.0 * r1["err"]).max() <= 1e-12 * sa
+    ru = compress(X, 0.0, 20)
+    ri = compress(X, 0.0, 20, weights=np.ones(120))
+    assert list(ru["pivots"]) == list(ri["pivots"])
+    assert np.abs(ru["err"] - ri["err"]).max() <= 1e-13 * ru["err"].max()
+
+
+W_PINS = [pin_w_indicator_definition, pin_w_bruteforce_tiny, pin_w_closed_form_orthogonal, pin_w_termination,
+          pin_w_scaling]
+
+
 FAST_PINS = [pin_orthonormal, pin_indicator_definition, pin_T_is_projection, pin_qr_equivalence,
              pin_bruteforce_tiny, pin_closed_form_orthogonal, pin_ties_lowest_index, pin_start_column,
              pin_exact_rank, pin_eckart_young, pin_nu_matches_indicator, pin_termination,

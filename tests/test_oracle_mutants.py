@@ -4,7 +4,8 @@ The oracle source carries compile-time hooks (RBD_ORACLE_MUTANT = k) that plant 
 mistake each; the default build has none.  This shows the pins are strong enough to catch a
 dropped re-orthogonalisation sweep, a wrong sign, a wrong tie-break, an ignored start column,
 a squared indicator, a missing normalisation, T taken from the unnormalised vector, a strict
-comparison in step 2.4, a squared Frobenius test and an off-by-one Gram-Schmidt loop.
+comparison in step 2.4, a squared Frobenius test, an off-by-one Gram-Schmidt loop, and under a
+diagonal A-norm the weights dropped from the indicator or from the step 2.2 test.
 """
 import functools
 
@@ -23,6 +24,8 @@ MUTANTS = {
     8: "step 2.4 uses a strict comparison",
     9: "Frobenius stop test on the squared norm",
     10: "Gram-Schmidt loop skips the last basis",
+    14: "A-norm indicator takes the Euclidean norm (weights dropped)",
+    15: "step 2.2 break test on the Euclidean norm under an A-norm",
 }
 
 
@@ -31,7 +34,7 @@ def test_mutant_is_caught(oracle_mod, mutant):
     oracle_mod.build(mutant)
     c = functools.partial(oracle_mod.compress, mutant=mutant)
     failed = []
-    for pin in pins.FAST_PINS + [pins.pin_paper_rank_functions]:
+    for pin in pins.FAST_PINS + [pins.pin_paper_rank_functions] + pins.W_PINS:
         try:
             pin(c)
         except (AssertionError, ValueError, IndexError, FloatingPointError) as e:

@@ -16,6 +16,18 @@ def test_pin(pin, compress):
     pin(compress)
 
 
+@pytest.mark.parametrize("pin", pins.W_PINS, ids=lambda p: p.__name__)
+def test_weighted_pin(pin, compress):
+    pin(compress)
+
+
+def test_weighted_invalid(oracle_mod):
+    X = np.ones((4, 3), order="F")
+    for w in (np.array([1.0, 0.0, 1.0, 1.0]), np.array([1.0, -2.0, 1.0, 1.0]), np.array([1.0, np.nan, 1.0, 1.0])):
+        with pytest.raises(ValueError, match="status 1"):
+            oracle_mod.compress(X, 0.0, 2, weights=w)
+
+
 def test_paper_rank_functions(compress):
     pins.pin_paper_rank_functions(compress)
 
