@@ -135,6 +135,36 @@ rbd_status rbd_compress(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64
                         void* stream, rbd_result* result);
 
 /*
+ * rbd_compress_weighted -- Algorithm 1 with the error measured in the A-norm of a diagonal
+ * A = diag(w) (Section 3.2, "general diagonal matrix": some components of each entry are to be
+ * kept better than others), ||v||_A = sqrt(sum_r w[r] v[r]^2).
+ *
+ *  Reading of the paper: the bases stay the Euclidean Gram-Schmidt bases of step 2.2 and
+ *  T = Y' X as in rbd_compress (the paper expands Y'AX and Y'AY to evaluate Eq. (evalerr) for
+ *  c = T(:, j), which an A-orthonormal basis would not need); the A-norm enters the indicator of
+ *  step 2.3 and the tolerance tests of steps 2.2 and 2.4.
+ *
+ *  w       [in]  device, m doubles, 8-byte aligned, each finite and > 0 (checked on the device:
+ *                RBD_EINVAL otherwise).  Read only; caller-owned.
+ *  Other arguments, outputs and errors as rbd_compress, with these differences:
+ *  err     [out] err[k] = max_j ||X(:, j) - Y(:, 0:k) T(0:k, j)||_A (certified: the A-norm of
+ *                the residual of the column that attains it, recomputed from X).
+ *  nu      [out] nu[k] stays the Euclidean ||v|| of step 2.2 that normalises xi_k.
+ *  tol     MAXCOL_ABS compares err with tol; MAXCOL_REL scales tol by max_j ||x_j||_A; FRO_REL
+ *          stops when sqrt(sum_j ||x_j - Y T(:, j)||_A^2) <= tol * sqrt(sum_j ||x_j||_A^2).
+ *  result  x_fro and x_maxcol are the A-norm values.
+ *  The numerical-rank floor of step 2.2 stays Euclidean.  The workspace is the one of
+ *  rbd_compress_workspace_bytes.  RBD_EUNSUPPORTED where the persistent loop kernel does not fit
+ *  (more than 512 rows per SM), since the A-norm form runs in that kernel only.
+ */
+rbd_status rbd_compress_weighted(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
+                                 const double* w, double tol, rbd_tol_mode mode, int64_t d_max,
+                                 int64_t start, double* Y, int64_t ldy, double* T, int64_t ldt,
+                                 int64_t* pivots, double* err, double* nu,
+                                 void* workspace, size_t workspace_bytes,
+                                 void* stream, rbd_result* result);
+
+/*
  * rbd_compress_resume -- continue a compression to a larger d_max: Algorithm 1's loop picks up
  * after d0 bases from its outputs (a checkpoint of the greedy state).
  *

@@ -28,8 +28,9 @@ static const int kLookahead = 4;
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms,
-               int pass_ctas_per_sm, int loop_max_smem) {
+               int pass_ctas_per_sm, int loop_max_smem, int wt) {
     w = Work{};
+    w.wt = wt;
     w.m = m;
     w.n = n;
     w.ldx = ldx;
@@ -61,8 +62,8 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
         const int64_t gl = std::min<int64_t>(num_sms, std::max<int64_t>(w.W, ceil_div(w.ldp, kLoopMaxRows)));
         const int64_t R = round_up(ceil_div(w.ldp, gl), 4);
         if (R <= kLoopMaxRows) {
-            const int LC = loop_chunk_cols_for(xt, (int)R);
-            const size_t smem = loop_smem_bytes(xt, (int)R, LC);
+            const int LC = loop_chunk_cols_for(xt, wt, (int)R);
+            const size_t smem = loop_smem_bytes(xt, wt, (int)R, LC);
             if (LC >= 4 && smem > 0 && smem <= (size_t)loop_max_smem) {
                 w.use_loop = 1;
                 w.G_loop = (int)gl;
@@ -110,12 +111,13 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     size_t o_v1 = take(lp ? 0 : ldp * 8), o_v2 = take(lp ? 0 : ldp * 8);
     size_t o_v1h = take(lp ? 0 : ldp * 4), o_v1l = take(lp ? 0 : ldp * 4);
     size_t o_v2s = take((size_t)w.NT * 2 * w.MT * 4);
+    size_t o_zs = take(lp ? (size_t)w.NT * 2 * w.MT * 4 : 0);
     size_t o_e = take((size_t)n * 8), o_xn2 = take((size_t)n * 8);
     size_t o_vpart = take(lp ? 0 : (size_t)w.LC_MAX * ldp * 8);
     size_t o_hpart = take((size_t)(lp ? w.G_loop : w.RC_MAX) * (size_t)d_max * 8);
     size_t o_h = take((size_t)d_max * 8);
-    size_t o_nu2 = take((size_t)std::max<int64_t>(w.RB, lp ? w.G_loop : 0) * 8);
-    size_t o_gslot = take((size_t)w.ngroups * (size_t)w.KMAX * (size_t)w.C * 8);
+    size_t o_nu2 = take((size_t)std::max<int64_t>(w.RB, lp ? 2 * (int64_t)w.G_loop : 0) * 8);
+    size_t o_gslot = take((size_t)(lp ? 2 : 1) * (size_t)w.ngroups * (size_t)w.KMAX * (size_t)w.C * 8);
     size_t o_gsum = take((size_t)w.ngroups * 8);
     size_t o_pbe = take(gp * 8), o_pbj = take(gp * 8);
     w.total_bytes = off;
@@ -133,6 +135,7 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     w.v1h = (float*)o_v1h;
     w.v1l = (float*)o_v1l;
     w.v2s = (float*)o_v2s;
+    w.zs = (float*)o_zs;
     w.e = (double*)o_e;
     w.xn2 = (double*)o_xn2;
     w.vpart = (double*)o_vpart;
@@ -163,6 +166,7 @@ void carve_work(Work& w, void* base) {
     RB_REBASE(v1h);
     RB_REBASE(v1l);
     RB_REBASE(v2s);
+    RB_REBASE(zs);
     RB_REBASE(e);
     RB_REBASE(xn2);
     RB_REBASE(vpart);
@@ -294,14 +298,18 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
                                   rbd_tol_mode mode, int64_t d_max, int64_t start, double* Y, int64_t ldy,
                                   double* T, int64_t ldt, int64_t* pivots, double* err, double* nu,
                                   void* workspace, size_t workspace_bytes, cudaStream_t st,
-                                  rbd_result* result, int64_t k0 = 0, int64_t next_pivot = 0) {
+                                  rbd_result* result, int64_t k0 = 0, int64_t next_pivot = 0,
+                                  const double* wts = nullptr) {
     DeviceState ds;
     cudaError_t ce = device_state(ds);
     if (ce != cudaSuccess) return map_cuda(ce);
     Work w;
-    if (!plan_work(w, m, n, ldx, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem))
+    if (!plan_work(w, m, n, ldx, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem,
+                   wts ? 1 : 0))
         return RBD_EUNSUPPORTED;
     if (xt == RBD_BF16 && !w.use_loop) return RBD_EUNSUPPORTED;  // BF16 runs in the persistent kernel only
+    if (wts && (!w.use_loop || k0 > 0)) return RBD_EUNSUPPORTED;  // the A-norm form: loop kernel, fresh runs
+    w.wts = wts;
 
     bool own = false;
     void* ws = workspace;
@@ -534,6 +542,17 @@ rbd_status rbd_compress(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64
     if (v != RBD_OK) return v;
     return compress_device(X, xt, m, n, ldx, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err, nu,
                            workspace, workspace_bytes, (cudaStream_t)stream, result);
+}
+
+rbd_status rbd_compress_weighted(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, const double* w,
+                                 double tol, rbd_tol_mode mode, int64_t d_max, int64_t start, double* Y, int64_t ldy,
+                                 double* T, int64_t ldt, int64_t* pivots, double* err, double* nu, void* workspace,
+                                 size_t workspace_bytes, void* stream, rbd_result* result) {
+    rbd_status v = validate(X, xt, m, n, ldx, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err);
+    if (v != RBD_OK) return v;
+    if (!w || ((uintptr_t)w & 7u) != 0) return RBD_EINVAL;
+    return compress_device(X, xt, m, n, ldx, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err, nu,
+                           workspace, workspace_bytes, (cudaStream_t)stream, result, 0, 0, w);
 }
 
 rbd_status rbd_compress_resume(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol,

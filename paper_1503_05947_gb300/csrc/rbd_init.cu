@@ -1,7 +1,8 @@
-// rbd_init.cu -- the initial pass over X (Section 3.3, "pre-computation of diag(X'AX)" with
-// A = I): e_j = ||X(:, j)||^2 for every column, ||X||_F and max_j ||X(:, j)|| for the
-// tolerance modes, and the one-time re-layout of X into the tile-major plane format the fused
-// pass streams with bulk copies (rbd_work.h).
+// rbd_init.cu -- the initial pass over X (Section 3.3, "pre-computation of diag(X'AX)"):
+// e_j = ||X(:, j)||_A^2 for every column (A = I, or A = diag(w) in the A-norm form, where the
+// Euclidean ||X(:, j)||^2 is kept as well for the numerical-rank floor), ||X||_F and
+// max_j ||X(:, j)|| in the same norm for the tolerance modes, and the one-time re-layout of X
+// into the tile-major plane format the fused pass streams with bulk copies (rbd_work.h).
 #include "rbd_device.cuh"
 #include "rbd_work.h"
 
@@ -16,6 +17,7 @@ struct InitParams {
     void* planes;
     double* e;
     double* xn2;
+    const double* wts;        // A = diag(wts), or nullptr for A = I
     Ctl* ctl;
     double tol;
     int mode;
@@ -55,7 +57,14 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
         const int64_t g = j / p.C;
         const int c = (int)(j % p.C);
         const bool live = j < p.n;
-        float s = 0.f, cc = 0.f;
+        float s = 0.f, cc = 0.f, sa = 0.f, ca = 0.f;
+        if (p.wts && j == 0) {
+            // the weights of A = diag(w) must be finite and positive
+            for (int64_t r = lane; r < p.m; r += 32) {
+                const double wr = p.wts[r];
+                if (!(isfinite(wr) && wr > 0.0)) bad = ST_EINVAL;
+            }
+        }
         for (int64_t r0 = 4 * lane; r0 < p.ldp; r0 += 128) {
             const int64_t t = r0 / p.MT;
             const int64_t rt = min((int64_t)p.MT, p.ldp - t * p.MT);
@@ -73,6 +82,18 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
                 if (!isfinite(x[q])) {
                     bad = ST_ENONFINITE;
                     x[q] = 0.0;
+                }
+            }
+            if (p.wts) {
+                // w_r x_r^2 as (w_r x_r) * x_r: the FP64 product split, times the split x_r
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t r = r0 + q;
+                    const double wx = (live && r < p.m) ? p.wts[r] * x[q] : 0.0;
+                    float xh, xl, wh, wl;
+                    split_double(x[q], xh, xl);
+                    split_double(wx, wh, wl);
+                    ff_mac2(sa, ca, xh, xl, wh, wl);
                 }
             }
             if (XT == 0) {
@@ -108,8 +129,9 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
             }
         }
         const double tsum = warp_sum_double(ff_to_double(s, cc));
+        const double asum = p.wts ? warp_sum_double(ff_to_double(sa, ca)) : tsum;
         if (live && lane == 0) {
-            p.e[j] = tsum;
+            p.e[j] = asum;
             p.xn2[j] = tsum;
         }
     }
@@ -128,7 +150,7 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
     const int64_t j0 = (p.n * t) / nt, j1 = (p.n * (t + 1)) / nt;
     double sum = 0.0, mx = 0.0;
     for (int64_t j = j0; j < j1; ++j) {
-        const double v = __ldcg(&p.xn2[j]);
+        const double v = __ldcg(p.wts ? &p.e[j] : &p.xn2[j]);
         sum += v;
         mx = fmax(mx, v);
     }
@@ -186,6 +208,7 @@ cudaError_t launch_init(const Work& w, const void* X, double tol, int mode, int6
     p.planes = w.planes;
     p.e = w.e;
     p.xn2 = w.xn2;
+    p.wts = w.wts;
     p.ctl = w.ctl;
     p.tol = tol;
     p.mode = mode;

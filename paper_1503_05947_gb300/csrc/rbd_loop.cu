@@ -21,12 +21,22 @@
 //   ---- grid barrier 4
 //   A    argmax over the CTAs (every CTA), Frobenius residual (fixed order)
 //
+// The A-norm form (Section 3.2, A = diag(w)) keeps this basis and T, and measures the indicator
+// in ||.||_A.  Adding xi_k changes ||r_j||_A^2 by -2 c_j xi_k' A r_j + c_j^2 xi_k' A xi_k, and
+// xi_k' A r_j = z' x_j with z = (I - Y Y')(w o xi_k) because r_j = (I - Y Y') x_j.  So the pass
+// takes a second dot product per element, with z, and three phases come before it:
+//   O3'  u = w o v2, ||v2||_A^2 partial, g_b = Y_b' u_b   (with O3, before barrier 3)
+//   D    E_cur and the tolerance tests take ||v2||_A
+//   O4   g = sum_b g_b, k / G coefficients per CTA;  ---- grid barrier 3b
+//   O5   z = u - Y g for this block's rows (nu is applied in the pass);  ---- grid barrier 3c
+//
 // This is classical Gram-Schmidt applied twice (see rbd_orth.cu for why, and for its accuracy);
 // Y is kept as a split FP32 copy stored ROW-BLOCK-MAJOR (block b = this CTA's R rows, all
 // columns contiguous), so each CTA streams only its own slice of Y, with bulk copies, and no
 // other CTA ever reads it.  X never changes, so the producer prefetches the first tiles of the
 // next pass while the orthogonalisation runs; only the pivot-vector tiles wait for O3.
 #include <algorithm>
+#include <type_traits>
 
 #include "rbd_device.cuh"
 #include "rbd_tile.cuh"
@@ -52,6 +62,7 @@ struct LoopParams {
     int64_t* pivots;
     double* err;
     double* nu_out;
+    const double* wts;    // A-norm form: the m weights of A = diag(wts)
     // workspace
     Ctl* ctl;
     uint32_t* bar;        // grid barrier {count, generation}
@@ -59,13 +70,15 @@ struct LoopParams {
     const double* xn2;
     float* ysb;           // [G][2][d_max][R] split Y, row-block-major
     float* v2s;           // tile-interleaved split v2 (pivot-vector tiles of the pass)
+    float* zs;            // A-norm form: tile-interleaved split z (second pivot vector)
     double* hpart;        // [G][d_max]
     double* h;            // [d_max]
-    double* nu2part;      // [G]
+    double* nu2part;      // [2 G]: ||v2||^2 partials, then (A-norm form) ||v2||_A^2 partials
     double* pbest_e;      // [G]
     int64_t* pbest_j;     // [G]
     uint32_t* gcnt;
     double* gslot;
+    double* gslot2;       // A-norm form: group partials of the dot products with z
     double* gsum;
     int R;                // rows per CTA block (multiple of 4, <= kLoopMaxRows)
     int LC;               // Y columns per streamed chunk (multiple of 4)
@@ -81,9 +94,9 @@ struct LoopSmem {
 // Ring stages per Y-chunk buffer: a chunk of a tall row block spans several stages, so that it
 // still holds about 32 columns of both planes (at most half the ring, so that two chunks are in
 // flight).
-template <int XT>
+template <class Cfg>
 __host__ __device__ inline int loop_ybuf_stages(int R) {
-    constexpr int S = TileCfg<XT>::S, STAGE = TileCfg<XT>::STAGE_FLOATS;
+    constexpr int S = Cfg::S, STAGE = Cfg::STAGE_FLOATS;
     int spb = (int)((32 * 2 * (int64_t)R + STAGE - 1) / STAGE);
     if (spb > S / 2) spb = S / 2;
     if (spb < 1) spb = 1;
@@ -91,17 +104,16 @@ __host__ __device__ inline int loop_ybuf_stages(int R) {
 }
 
 // Y columns per chunk: both planes of LC x R floats fill one Y-chunk buffer.
-template <int XT>
+template <class Cfg>
 __host__ __device__ inline int loop_chunk_cols(int R) {
-    int lc = (loop_ybuf_stages<XT>(R) * TileCfg<XT>::STAGE_FLOATS / 2) / R;
+    int lc = (loop_ybuf_stages<Cfg>(R) * Cfg::STAGE_FLOATS / 2) / R;
     lc &= ~3;
     if (lc > 256) lc = 256;
     return lc;
 }
 
-template <int XT>
+template <class Cfg>
 __host__ __device__ inline LoopSmem loop_smem_layout(int R, int LC) {
-    using Cfg = TileCfg<XT>;
     LoopSmem s;
     size_t o = (size_t)Cfg::S * Cfg::STAGE_FLOATS * 4;  // the ring: pass stages / Y chunks
     s.bars = o;
@@ -247,9 +259,14 @@ __device__ __forceinline__ void ystream_end_step(YStream& ys) {
     }
 }
 
-template <int XT>
+// The storage type XT fixes the tile shape; WT selects the A-norm form (Section 3.2, A = diag(w)):
+// a second pivot vector z = (I - Y Y')(w o v2) in the pass and three more phases per basis.
+template <int XT, bool WT>
+using LoopCfg = std::conditional_t<WT, TileCfgW<XT>, TileCfg<XT>>;
+
+template <int XT, bool WT>
 __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParams p) {
-    using Cfg = TileCfg<XT>;
+    using Cfg = LoopCfg<XT, WT>;
     constexpr int UB = Cfg::PL * Cfg::ESIZE;  // X bytes per element and column of a unit
     constexpr int NW = Cfg::NW, CPW = Cfg::CPW, C = Cfg::C, MT = Cfg::MT, S = Cfg::S;
     constexpr int XI = Cfg::XI_FLOATS, STAGE = Cfg::STAGE_FLOATS;
@@ -257,7 +274,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     constexpr int MAXRPT = kLoopMaxRows / NCONS;  // rows per consumer thread when R > NCONS
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const LoopSmem L = loop_smem_layout<XT>(p.R, p.LC);
+    const LoopSmem L = loop_smem_layout<Cfg>(p.R, p.LC);
     float* stages = reinterpret_cast<float*>(smem_raw);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bars);
     uint64_t* empty = full + S;
@@ -300,8 +317,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     uint32_t gen = 0;
     YStream ys;
     ys.ring = stages;
-    ys.buf_floats = loop_ybuf_stages<XT>(R) * STAGE;
-    ys.NB = S / loop_ybuf_stages<XT>(R);
+    ys.buf_floats = loop_ybuf_stages<Cfg>(R) * STAGE;
+    ys.NB = S / loop_ybuf_stages<Cfg>(R);
     ys.ybar = ybar;
     ys.coef = coef;
     ys.ysb_b = p.ysb + b * 2 * p.d_max * (int64_t)R;
@@ -336,11 +353,140 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     int32_t stop = STOP_NONE;
     double nu = 0.0;
     for (;; ++k) {
-        // ---------------- O1 / O1': v1 = x_i - Y t, partial h = Y_b' v1_b ----------------
         const int NSUB = (R <= NCONS) ? (NCONS / R) : 1;
         const int q = (R <= NCONS) ? (tid / R) : 0;
         const int rfirst = (R <= NCONS) ? (tid % R) : tid;
         const bool active = (warp < NW) && ((R <= NCONS) ? (tid < NSUB * R) : true);
+
+        // out[b][l] = Y_b(:, l)' s_b for l < k, s_b = (v1h, v1l) of this block's rows (consumers).
+        // tpc consecutive threads share a column, each summing every tpc-th row in two interleaved
+        // chains; the parts are combined in float-float inside the group of lanes.  tpc (a power
+        // of two <= 32) minimises rounds x (rows per thread + combine steps).
+        auto block_dots = [&](double* out) {
+            ystream<NCONS>(
+                ys, k, 2, tid, ctl, [&](int64_t, float& hi, float& lo) { hi = lo = 0.f; },
+                [&](const float* yh, const float* yl, const float*, const float*, int64_t l0, int lc) {
+                    int tpc = 1, best = 1 << 30;
+                    for (int tq = 1, lg = 0; tq <= 32; tq <<= 1, ++lg) {
+                        const int cost = ((lc + NCONS / tq - 1) / (NCONS / tq)) * ((Rb + tq - 1) / tq + 2 * lg);
+                        if (cost < best) {
+                            best = cost;
+                            tpc = tq;
+                        }
+                    }
+                    const int per = NCONS / tpc;
+                    for (int lb = 0; lb < lc; lb += per) {
+                        const int l = lb + tid / tpc, qq = tid % tpc;
+                        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+                        if (l < lc) {
+                            const float* ch = yh + l * R;
+                            const float* cl = yl + l * R;
+                            int r = qq;
+                            for (; r + tpc < Rb; r += 2 * tpc) {
+                                ff_mac2(s0, c0, ch[r], cl[r], v1h[r], v1l[r]);
+                                ff_mac2(s1, c1, ch[r + tpc], cl[r + tpc], v1h[r + tpc], v1l[r + tpc]);
+                            }
+                            if (r < Rb) ff_mac2(s0, c0, ch[r], cl[r], v1h[r], v1l[r]);
+                            ff_add(s0, c0, s1, c1);
+                        }
+                        for (int o = 1; o < tpc; o <<= 1) {
+                            const float s2 = __shfl_xor_sync(0xffffffffu, s0, o);
+                            const float c2 = __shfl_xor_sync(0xffffffffu, c0, o);
+                            ff_add(s0, c0, s2, c2);
+                        }
+                        if (l < lc && qq == 0) out[b * p.d_max + l0 + l] = ff_to_double(s0, c0);
+                    }
+                });
+        };
+        // dst[r] = v1s[r] - sum_{l<k} Y_b(r, l) coefv[l] for this block's rows (consumers; dst may be
+        // v1s).  Float-float: when the pivot nearly lies in span(Y), v1 is tiny and the coefficients
+        // are not small relative to it, so Y h needs the full precision for Y'Y = I to hold.
+        auto block_sub = [&](const double* coefv, double* dst) {
+            float as[MAXRPT], ac[MAXRPT];
+#pragma unroll
+            for (int i = 0; i < MAXRPT; ++i) as[i] = ac[i] = 0.f;
+            if (k > 0) {
+                ystream<NCONS>(
+                    ys, k, 2, tid, ctl,
+                    [&](int64_t l, float& hi, float& lo) { split_double(__ldcg(&coefv[l]), hi, lo); },
+                    [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
+                        if (!active) return;
+#pragma unroll
+                        for (int i = 0; i < MAXRPT; ++i) {
+                            const int r = rfirst + i * NCONS;
+                            if (r >= Rb || (R <= NCONS && i > 0)) break;
+                            for (int l = q; l < lc; l += NSUB)
+                                ff_mac2(as[i], ac[i], yh[l * R + r], yl[l * R + r], ch[l], cl[l]);
+                        }
+                    });
+            }
+            if (R <= NCONS) {
+                if (active) part[q * R + rfirst] = ff_to_double(as[0], ac[0]);
+                named_bar(1, NCONS);
+                for (int r = tid; r < R; r += NCONS) {
+                    double corr = 0.0;
+                    for (int qq = 0; qq < NSUB; ++qq) corr += part[qq * R + r];
+                    dst[r] = (r < Rb) ? v1s[r] - corr : 0.0;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < MAXRPT; ++i) {
+                    const int r = rfirst + i * NCONS;
+                    if (r >= R) break;
+                    dst[r] = (r < Rb) ? v1s[r] - ff_to_double(as[i], ac[i]) : 0.0;
+                }
+            }
+            named_bar(1, NCONS);
+        };
+        // split copy of this block's rows of src for the pass: tile t of dstv holds
+        // [hi(rows_t) | lo(rows_t)] at t * 2 * MT (consumers).
+        auto write_split = [&](const double* src, float* dstv) {
+            for (int r = tid; r < Rb; r += NCONS) {
+                const int64_t row = r0 + r;
+                const int64_t t = row / MT;
+                const int64_t rt = min((int64_t)MT, p.ldp - t * MT);
+                const int64_t off = t * 2 * MT + (row - t * MT);
+                float hi, lo;
+                split_double(src[r], hi, lo);
+                dstv[off] = hi;
+                dstv[off + rt] = lo;
+            }
+            fence_proxy_async_global();  // read by bulk copies in the pass
+        };
+        // producer: the X tiles of pass k (the ring is free once every consumer is done with Y);
+        // X never changes, so its first tiles load while the CTAs synchronise.
+        auto prefetch_x = [&]() {
+            if (warp != NW || lane != 0 || k >= p.d_max || !ok) return;
+            npref = min(nunits, (int64_t)S);
+            pf_s0 = ps;
+            pf_ph0 = pph;
+            int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
+            for (int64_t i = 0; i < npref; ++i) {
+                if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                    raise_status(ctl, ST_ETIMEOUT);
+                    ok = false;
+                    npref = i;
+                    break;
+                }
+                const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                const uint32_t x_bytes = (uint32_t)(C * UB) * rows;
+                float* st = stages + (size_t)ps * STAGE;
+                mbar_arrive_expect_tx(&full[ps], x_bytes);
+                bulk_g2s(st + XI, planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE, x_bytes, &full[ps],
+                         pol_x);
+                if (++ps == S) {
+                    ps = 0;
+                    pph ^= 1u;
+                    preuse = true;
+                }
+                if (++t == NT) {
+                    t = 0;
+                    ++g;
+                }
+            }
+        };
+
+        // ---------------- O1 / O1': v1 = x_i - Y t, partial h = Y_b' v1_b ----------------
         if (warp < NW) {
             // the pivot column's rows of this block, loaded now so the loads overlap the stream
             // (v2own is free until O3; each thread later reads back only the rows it loaded)
@@ -391,46 +537,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 }
             }
             named_bar(1, NCONS);
-            if (k > 0) {
-                ystream<NCONS>(
-                    ys, k, 2, tid, ctl, [&](int64_t, float& hi, float& lo) { hi = lo = 0.f; },
-                    [&](const float* yh, const float* yl, const float*, const float*, int64_t l0, int lc) {
-                        // tpc consecutive threads share a column, each summing every tpc-th row in
-                        // two interleaved chains; the parts are combined in float-float inside the
-                        // group of lanes.  tpc (a power of two <= 32) minimises rounds x (rows per
-                        // thread + combine steps).
-                        int tpc = 1, best = 1 << 30;
-                        for (int tq = 1, lg = 0; tq <= 32; tq <<= 1, ++lg) {
-                            const int cost = ((lc + NCONS / tq - 1) / (NCONS / tq)) * ((Rb + tq - 1) / tq + 2 * lg);
-                            if (cost < best) {
-                                best = cost;
-                                tpc = tq;
-                            }
-                        }
-                        const int per = NCONS / tpc;
-                        for (int lb = 0; lb < lc; lb += per) {
-                            const int l = lb + tid / tpc, qq = tid % tpc;
-                            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
-                            if (l < lc) {
-                                const float* ch = yh + l * R;
-                                const float* cl = yl + l * R;
-                                int r = qq;
-                                for (; r + tpc < Rb; r += 2 * tpc) {
-                                    ff_mac2(s0, c0, ch[r], cl[r], v1h[r], v1l[r]);
-                                    ff_mac2(s1, c1, ch[r + tpc], cl[r + tpc], v1h[r + tpc], v1l[r + tpc]);
-                                }
-                                if (r < Rb) ff_mac2(s0, c0, ch[r], cl[r], v1h[r], v1l[r]);
-                                ff_add(s0, c0, s1, c1);
-                            }
-                            for (int o = 1; o < tpc; o <<= 1) {
-                                const float s2 = __shfl_xor_sync(0xffffffffu, s0, o);
-                                const float c2 = __shfl_xor_sync(0xffffffffu, c0, o);
-                                ff_add(s0, c0, s2, c2);
-                            }
-                            if (l < lc && qq == 0) p.hpart[b * p.d_max + l0 + l] = ff_to_double(s0, c0);
-                        }
-                    });
-            }
+            if (k > 0) block_dots(p.hpart);
         }
         if (k > 0) {
             if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;   // barrier 1
@@ -451,127 +558,75 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
         }
 
         // ---------------- O3: v2 = v1 - Y h, ||v2||^2 partial ----------------
-        // float-float as in O1: when the pivot nearly lies in span(Y), ||v1|| is tiny and h is
-        // not small relative to it, so Y h needs the full precision for Y'Y = I to hold.
         if (warp < NW) {
-            float as[MAXRPT], ac[MAXRPT];
-#pragma unroll
-            for (int i = 0; i < MAXRPT; ++i) as[i] = ac[i] = 0.f;
-            if (k > 0) {
-                ystream<NCONS>(
-                    ys, k, 2, tid, ctl,
-                    [&](int64_t l, float& hi, float& lo) { split_double(__ldcg(&p.h[l]), hi, lo); },
-                    [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
-                        if (!active) return;
-#pragma unroll
-                        for (int i = 0; i < MAXRPT; ++i) {
-                            const int r = rfirst + i * NCONS;
-                            if (r >= Rb || (R <= NCONS && i > 0)) break;
-                            for (int l = q; l < lc; l += NSUB)
-                                ff_mac2(as[i], ac[i], yh[l * R + r], yl[l * R + r], ch[l], cl[l]);
-                        }
-                    });
-            }
-            if (R <= NCONS) {
-                if (active) part[q * R + rfirst] = ff_to_double(as[0], ac[0]);
-                named_bar(1, NCONS);
-                for (int r = tid; r < R; r += NCONS) {
-                    double corr = 0.0;
-                    for (int qq = 0; qq < NSUB; ++qq) corr += part[qq * R + r];
-                    v2own[r] = (r < Rb) ? v1s[r] - corr : 0.0;
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < MAXRPT; ++i) {
-                    const int r = rfirst + i * NCONS;
-                    if (r >= R) break;
-                    v2own[r] = (r < Rb) ? v1s[r] - ff_to_double(as[i], ac[i]) : 0.0;
-                }
-            }
-            named_bar(1, NCONS);
-            // split copy for the pass (tile-interleaved), and ||v2||^2 of this block (fixed order)
-            for (int r = tid; r < Rb; r += NCONS) {
-                const int64_t row = r0 + r;
-                const int64_t t = row / MT;
-                const int64_t rt = min((int64_t)MT, p.ldp - t * MT);
-                const int64_t off = t * 2 * MT + (row - t * MT);
-                float hi, lo;
-                split_double(v2own[r], hi, lo);
-                p.v2s[off] = hi;
-                p.v2s[off + rt] = lo;
-            }
-            fence_proxy_async_global();  // v2s is read by bulk copies in the pass
+            block_sub(p.h, v2own);
+            write_split(v2own, p.v2s);
             if (warp == 0) {
                 double acc = 0.0;
                 for (int r = lane; r < Rb; r += 32) acc += v2own[r] * v2own[r];
                 acc = warp_sum_double(acc);
                 if (lane == 0) p.nu2part[b] = acc;
             }
-        }
-        // ---------------- producer: prefetch the X tiles of pass k ----------------
-        // The ring is free once every consumer is past O3; X never changes, so its first tiles
-        // load while the CTAs synchronise and take the stop decision.
-        ystream_end_step(ys);
-        __syncthreads();
-        if (warp == NW) {
-            if (lane == 0 && k < p.d_max && ok) {
-                npref = min(nunits, (int64_t)S);
-                pf_s0 = ps;
-                pf_ph0 = pph;
-                int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
-                for (int64_t i = 0; i < npref; ++i) {
-                    if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
-                        raise_status(ctl, ST_ETIMEOUT);
-                        ok = false;
-                        npref = i;
-                        break;
-                    }
-                    const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
-                    const uint32_t x_bytes = (uint32_t)(C * UB) * rows;
-                    float* st = stages + (size_t)ps * STAGE;
-                    mbar_arrive_expect_tx(&full[ps], x_bytes);
-                    bulk_g2s(st + XI, planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE, x_bytes, &full[ps],
-                             pol_x);
-                    if (++ps == S) {
-                        ps = 0;
-                        pph ^= 1u;
-                        preuse = true;
-                    }
-                    if (++t == NT) {
-                        t = 0;
-                        ++g;
-                    }
+            if constexpr (WT) {
+                // ||v2||_A^2 of this block (fixed order), u = w o v2 (kept in v1s and split in
+                // v1h / v1l, free after O3) and the partial g_b = Y_b' u_b
+                if (warp == 1) {
+                    double acc = 0.0;
+                    for (int r = lane; r < Rb; r += 32)
+                        if (r0 + r < p.m) acc += __ldg(&p.wts[r0 + r]) * (v2own[r] * v2own[r]);
+                    acc = warp_sum_double(acc);
+                    if (lane == 0) p.nu2part[G + b] = acc;
                 }
+                for (int r = tid; r < R; r += NCONS) {
+                    const double u = (r < Rb && r0 + r < p.m) ? __ldg(&p.wts[r0 + r]) * v2own[r] : 0.0;
+                    v1s[r] = u;
+                    split_double(u, v1h[r], v1l[r]);
+                }
+                named_bar(1, NCONS);
+                if (k > 0) block_dots(p.hpart);
             }
+        }
+        if constexpr (!WT) {
+            ystream_end_step(ys);
+            __syncthreads();
+            prefetch_x();
         }
         if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 3
         if (!ok || __ldcg(&ctl->status) != 0) break;
 
         // ---------------- D: nu, certified E_cur of basis k-1, stop tests ----------------
+        // A-norm form: E_cur and the tests of steps 2.2 / 2.4 take ||v2||_A; xi = v2 / nu and the
+        // numerical-rank floor stay Euclidean.
         if (warp == 0) {
-            double acc = 0.0;
+            double acc = 0.0, acc2 = 0.0;
             #pragma unroll 8
-            for (int64_t bb = lane; bb < G; bb += 32) acc += __ldcg(&p.nu2part[bb]);
+            for (int64_t bb = lane; bb < G; bb += 32) {
+                acc += __ldcg(&p.nu2part[bb]);
+                if constexpr (WT) acc2 += __ldcg(&p.nu2part[G + bb]);
+            }
             acc = warp_sum_double(acc);
+            if constexpr (WT) acc2 = warp_sum_double(acc2);
             if (lane == 0) {
                 const double nuv = sqrt(acc);
+                const double nea = WT ? sqrt(acc2) : nuv;
                 const double xin = sqrt(p.xn2[piv]);
                 int32_t st = STOP_NONE;
                 if (k > 0) {
                     if (mode == MODE_FRO_REL) {
                         if (__ldcg(&ctl->fro_last) <= fro_tol) st = STOP_TOL;
-                    } else if (nuv <= eps_r) {
+                    } else if (nea <= eps_r) {
                         st = STOP_TOL;
                     }
                 }
                 if (st == STOP_NONE && k >= p.d_max) st = STOP_DMAX;
-                if (st == STOP_NONE && (nuv < eps_r22 || nuv <= kRankFloor * xin)) st = STOP_BREAK;
+                if (st == STOP_NONE && (nea < eps_r22 || nuv <= kRankFloor * xin)) st = STOP_BREAK;
                 bcast[0] = nuv;
+                bcast[3] = (WT && acc > 0.0) ? acc2 / acc : 1.0;  // xi' A xi
                 sflags[1] = st;
                 if (b == 0) {
                     if (k > 0) {
-                        p.err[k - 1] = nuv;
-                        ctl->err_last = nuv;
+                        p.err[k - 1] = nea;
+                        ctl->err_last = nea;
                     }
                     if (st == STOP_NONE) {
                         p.pivots[k] = piv;
@@ -582,8 +637,37 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
         }
         __syncthreads();
         nu = bcast[0];
+        const double qa = bcast[3];
         stop = sflags[1];
         if (stop != STOP_NONE) break;
+
+        if constexpr (WT) {
+            // ---------------- O4: g(l) = sum_b g_b(l), k / G coefficients per CTA ----------------
+            if (k > 0) {
+                if (warp < NW) {
+                    const int64_t lb0 = (k * b) / G, lb1 = (k * (b + 1)) / G;
+                    for (int64_t l = lb0 + warp; l < lb1; l += NW) {
+                        double acc = 0.0;
+                        #pragma unroll 8
+                        for (int64_t bb = lane; bb < G; bb += 32) acc += __ldcg(&p.hpart[bb * p.d_max + l]);
+                        acc = warp_sum_double(acc);
+                        if (lane == 0) p.h[l] = acc;
+                    }
+                }
+                if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 3b
+                if (!ok || __ldcg(&ctl->status) != 0) break;
+            }
+            // ---------------- O5: z = u - Y g for this block's rows ----------------
+            if (warp < NW) {
+                block_sub(p.h, v1s);
+                write_split(v1s, p.zs);
+            }
+            ystream_end_step(ys);
+            __syncthreads();
+            prefetch_x();
+            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 3c
+            if (!ok || __ldcg(&ctl->status) != 0) break;
+        }
 
         // ---------------- P: the fused pass of basis k ----------------
         const double inv_nu = 1.0 / nu;
@@ -605,8 +689,10 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 for (int64_t i = 0; i < npref; ++i) {
                     const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
                     const uint32_t xi_bytes = 2u * rows * 4u;
-                    mbar_arrive_expect_tx(&full[sp], xi_bytes);
+                    mbar_arrive_expect_tx(&full[sp], WT ? 2u * xi_bytes : xi_bytes);
                     bulk_g2s(stages + (size_t)sp * STAGE, p.v2s + t * 2 * MT, xi_bytes, &full[sp], pol_xi);
+                    if constexpr (WT)
+                        bulk_g2s(stages + (size_t)sp * STAGE + 2 * MT, p.zs + t * 2 * MT, xi_bytes, &full[sp], pol_xi);
                     if (++sp == S) sp = 0;
                     if (++t == NT) {
                         t = 0;
@@ -626,8 +712,9 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                     mbar_arrive_expect_tx(&full[ps], x_bytes);
                     bulk_g2s(st + XI, planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE, x_bytes, &full[ps],
                              pol_x);
-                    mbar_arrive_expect_tx(&full[ps], xi_bytes);
+                    mbar_arrive_expect_tx(&full[ps], WT ? 2u * xi_bytes : xi_bytes);
                     bulk_g2s(st, p.v2s + t * 2 * MT, xi_bytes, &full[ps], pol_xi);
+                    if constexpr (WT) bulk_g2s(st + 2 * MT, p.zs + t * 2 * MT, xi_bytes, &full[ps], pol_xi);
                     if (++ps == S) {
                         ps = 0;
                         pph ^= 1u;
@@ -643,10 +730,15 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
         } else {
             // consumers
             float acc_s[CPW][4], acc_c[CPW][4];
+            float acc2_s[WT ? CPW : 1][4], acc2_c[WT ? CPW : 1][4];  // A-norm form: dots with z
 #pragma unroll
             for (int qq = 0; qq < CPW; ++qq)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
+#pragma unroll
+            for (int qq = 0; qq < (WT ? CPW : 1); ++qq)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc2_s[qq][e] = acc2_c[qq][e] = 0.f;
             double best_e = -1.0;
             int64_t best_j = INT64_MAX;
             double e_old[CPW];
@@ -661,8 +753,10 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             fc.k = k;
             fc.piv = piv;
             fc.inv_nu = inv_nu;
+            fc.q = qa;
             fc.gcnt = p.gcnt;
             fc.gslot = p.gslot;
+            fc.gslot2 = p.gslot2;
             fc.gsum = p.gsum;
             fc.KMAX = p.KMAX;
             fc.W = W;
@@ -702,7 +796,22 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 const int rows = (int)min((int64_t)MT, p.ldp - t * MT);
                 if (ok) {
                     const float* st = stages + (size_t)s * STAGE;
+                    if constexpr (WT) {
                         if constexpr (XT == 2) {
+                            if (rows == MT)
+                                consume_tile_bf16_w<CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c, acc2_s, acc2_c);
+                            else
+                                consume_tile_bf16_w<CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c, acc2_s,
+                                                                    acc2_c);
+                        } else {
+                            if (rows == MT)
+                                consume_tile_w<Cfg::PL, CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c, acc2_s,
+                                                                       acc2_c);
+                            else
+                                consume_tile_w<Cfg::PL, CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c, acc2_s,
+                                                                        acc2_c);
+                        }
+                    } else if constexpr (XT == 2) {
                         if (rows == MT)
                             consume_tile_bf16<CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
                         else
@@ -717,7 +826,11 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
                 if (t != NT - 1 && u != L1 - 1) continue;
-                flush_group<CPW, C, NCONS>(fc, g, warp, lane, tid, acc_s, acc_c, e_old, best_e, best_j, gbuf);
+                if constexpr (WT)
+                    flush_group_t<CPW, C, NCONS, true>(fc, g, warp, lane, tid, acc_s, acc_c, acc2_s, acc2_c, e_old,
+                                                       best_e, best_j, gbuf);
+                else
+                    flush_group<CPW, C, NCONS>(fc, g, warp, lane, tid, acc_s, acc_c, e_old, best_e, best_j, gbuf);
             }
             if (lane == 0) {
                 red_e[warp] = best_e;
@@ -813,26 +926,32 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     }
 }
 
-int loop_chunk_cols_for(int xt, int R) {
-    if (xt == 0) return loop_chunk_cols<0>(R);
-    if (xt == 1) return loop_chunk_cols<1>(R);
-    if (xt == 2) return loop_chunk_cols<2>(R);
+int loop_chunk_cols_for(int xt, int wt, int R) {
+    if (xt == 0) return wt ? loop_chunk_cols<LoopCfg<0, true>>(R) : loop_chunk_cols<LoopCfg<0, false>>(R);
+    if (xt == 1) return wt ? loop_chunk_cols<LoopCfg<1, true>>(R) : loop_chunk_cols<LoopCfg<1, false>>(R);
+    if (xt == 2) return wt ? loop_chunk_cols<LoopCfg<2, true>>(R) : loop_chunk_cols<LoopCfg<2, false>>(R);
     return 0;
 }
 
-size_t loop_smem_bytes(int xt, int R, int LC) {
-    if (xt == 0) return loop_smem_layout<0>(R, LC).total;
-    if (xt == 1) return loop_smem_layout<1>(R, LC).total;
-    if (xt == 2) return loop_smem_layout<2>(R, LC).total;
+size_t loop_smem_bytes(int xt, int wt, int R, int LC) {
+    if (xt == 0) return wt ? loop_smem_layout<LoopCfg<0, true>>(R, LC).total : loop_smem_layout<LoopCfg<0, false>>(R, LC).total;
+    if (xt == 1) return wt ? loop_smem_layout<LoopCfg<1, true>>(R, LC).total : loop_smem_layout<LoopCfg<1, false>>(R, LC).total;
+    if (xt == 2) return wt ? loop_smem_layout<LoopCfg<2, true>>(R, LC).total : loop_smem_layout<LoopCfg<2, false>>(R, LC).total;
     return 0;
+}
+
+static const void* loop_fn(int xt, int wt) {
+    if (wt) return (xt == 0) ? (const void*)loop_kernel<0, true> : (xt == 1) ? (const void*)loop_kernel<1, true>
+                                                                              : (const void*)loop_kernel<2, true>;
+    return (xt == 0) ? (const void*)loop_kernel<0, false> : (xt == 1) ? (const void*)loop_kernel<1, false>
+                                                                      : (const void*)loop_kernel<2, false>;
 }
 
 cudaError_t loop_kernel_setup(int max_smem) {
-    cudaError_t e = cudaFuncSetAttribute(loop_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(loop_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(loop_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    cudaError_t e = cudaSuccess;
+    for (int wt = 0; wt < 2 && e == cudaSuccess; ++wt)
+        for (int xt = 0; xt < 3 && e == cudaSuccess; ++xt)
+            e = cudaFuncSetAttribute(loop_fn(xt, wt), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     return e;
 }
 
@@ -862,12 +981,14 @@ cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, do
     p.pivots = pivots;
     p.err = err;
     p.nu_out = nu_out;
+    p.wts = w.wts;
     p.ctl = w.ctl;
     p.bar = w.ctl->bar;
     p.e = w.e;
     p.xn2 = w.xn2;
     p.ysb = w.ysb;
     p.v2s = w.v2s;
+    p.zs = w.zs;
     p.hpart = w.hpart;
     p.h = w.h;
     p.nu2part = w.nu2part;
@@ -875,13 +996,13 @@ cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, do
     p.pbest_j = w.pbest_j;
     p.gcnt = w.gcnt;
     p.gslot = w.gslot;
+    p.gslot2 = w.gslot + (size_t)w.ngroups * (size_t)w.KMAX * (size_t)w.C;
     p.gsum = w.gsum;
     p.R = w.R;
     p.LC = w.LC;
     void* args[] = {&p};
-    const void* fn = (w.xt == 0)   ? (const void*)loop_kernel<0>
-                     : (w.xt == 1) ? (const void*)loop_kernel<1>
-                                   : (const void*)loop_kernel<2>;
+    if (w.wt && !w.wts) return cudaErrorInvalidValue;
+    const void* fn = loop_fn(w.xt, w.wt);
     const int threads = (w.xt == 0) ? TileCfg<0>::THREADS : (w.xt == 1) ? TileCfg<1>::THREADS : TileCfg<2>::THREADS;
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)w.G_loop), dim3((unsigned)threads), args, w.loop_smem, st);
 }

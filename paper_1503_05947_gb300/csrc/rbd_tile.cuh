@@ -3,6 +3,7 @@
 //
 //   c_j = xi_k' X(:, j)   (step 2.2, T(k, j) = c_j)
 //   e_j <- e_j - c_j^2    (Eq. (evalerr) with A = I and orthonormal Y: ||x||^2 - ||c||^2)
+//   A = diag(w): e_j <- e_j - c_j (2 b_j - c_j xi_k' A xi_k), b_j = z' x_j, z = (I - Y Y')(w o xi_k)
 //   argmax_j e_j          (step 2.3; lowest j on ties)
 #pragma once
 
@@ -47,6 +48,52 @@ __device__ __forceinline__ void consume_tile(const float* __restrict__ st, int r
                 ff_mac1(acc_s[q][1], acc_c[q][1], a.y, zh.y, zl.y);
                 ff_mac1(acc_s[q][2], acc_c[q][2], a.z, zh.z, zl.z);
                 ff_mac1(acc_s[q][3], acc_c[q][3], a.w, zh.w, zl.w);
+            }
+        }
+    }
+}
+
+// The A-norm form (Section 3.2): two dot products per column and row, with xi (acc) and with
+// z = (I - Y Y')(w o xi) (acc2).  Stage layout: [xi hi | xi lo | z hi (at 2 MT) | z lo | pad to
+// 4*MT | column c plane p at (c*P + p)*rows].
+template <int P, int CPW, int MT, bool FULL>
+__device__ __forceinline__ void consume_tile_w(const float* __restrict__ st, int rows, int warp, int lane,
+                                               float (&acc_s)[CPW][4], float (&acc_c)[CPW][4],
+                                               float (&acc2_s)[CPW][4], float (&acc2_c)[CPW][4]) {
+    constexpr int XI = 4 * MT;
+    const int R = FULL ? MT : rows;
+    const int nsl = FULL ? MT / 128 : (rows >> 7);
+#pragma unroll
+    for (int sl = 0; sl < MT / 128; ++sl) {
+        if (!FULL && sl >= nsl) break;
+        const int off = sl * 128 + lane * 4;
+        const float4 zh = *reinterpret_cast<const float4*>(st + off);
+        const float4 zl = *reinterpret_cast<const float4*>(st + R + off);
+        const float4 wh = *reinterpret_cast<const float4*>(st + 2 * MT + off);
+        const float4 wl = *reinterpret_cast<const float4*>(st + 2 * MT + R + off);
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+            const float* col = st + XI + (warp * CPW + q) * P * R + off;
+            const float4 a = *reinterpret_cast<const float4*>(col);
+            if (P == 2) {
+                const float4 al = *reinterpret_cast<const float4*>(col + R);
+                ff_mac2(acc_s[q][0], acc_c[q][0], a.x, al.x, zh.x, zl.x);
+                ff_mac2(acc_s[q][1], acc_c[q][1], a.y, al.y, zh.y, zl.y);
+                ff_mac2(acc_s[q][2], acc_c[q][2], a.z, al.z, zh.z, zl.z);
+                ff_mac2(acc_s[q][3], acc_c[q][3], a.w, al.w, zh.w, zl.w);
+                ff_mac2(acc2_s[q][0], acc2_c[q][0], a.x, al.x, wh.x, wl.x);
+                ff_mac2(acc2_s[q][1], acc2_c[q][1], a.y, al.y, wh.y, wl.y);
+                ff_mac2(acc2_s[q][2], acc2_c[q][2], a.z, al.z, wh.z, wl.z);
+                ff_mac2(acc2_s[q][3], acc2_c[q][3], a.w, al.w, wh.w, wl.w);
+            } else {
+                ff_mac1(acc_s[q][0], acc_c[q][0], a.x, zh.x, zl.x);
+                ff_mac1(acc_s[q][1], acc_c[q][1], a.y, zh.y, zl.y);
+                ff_mac1(acc_s[q][2], acc_c[q][2], a.z, zh.z, zl.z);
+                ff_mac1(acc_s[q][3], acc_c[q][3], a.w, zh.w, zl.w);
+                ff_mac1(acc2_s[q][0], acc2_c[q][0], a.x, wh.x, wl.x);
+                ff_mac1(acc2_s[q][1], acc2_c[q][1], a.y, wh.y, wl.y);
+                ff_mac1(acc2_s[q][2], acc2_c[q][2], a.z, wh.z, wl.z);
+                ff_mac1(acc2_s[q][3], acc2_c[q][3], a.w, wh.w, wl.w);
             }
         }
     }
@@ -124,6 +171,51 @@ __device__ __forceinline__ void consume_tile_bf16(const float* __restrict__ st, 
     }
 }
 
+// BF16 storage in the A-norm form: as consume_tile_bf16, a second FP32 sum with the leading part
+// of z (stage layout of consume_tile_w).
+template <int CPW, int MT, bool FULL>
+__device__ __forceinline__ void consume_tile_bf16_w(const float* __restrict__ st, int rows, int warp, int lane,
+                                                    float (&acc_s)[CPW][4], float (&acc_c)[CPW][4],
+                                                    float (&acc2_s)[CPW][4], float (&acc2_c)[CPW][4]) {
+    constexpr int XI = 4 * MT;
+    const int R = FULL ? MT : rows;
+    const int nsl = FULL ? MT / 128 : (rows >> 7);
+    const unsigned short* xb = reinterpret_cast<const unsigned short*>(st + XI);
+    float part[CPW][4], part2[CPW][4];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) part[q][e] = part2[q][e] = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < MT / 128; ++sl) {
+        if (!FULL && sl >= nsl) break;
+        const int off = sl * 128 + lane * 4;
+        const float4 zh = *reinterpret_cast<const float4*>(st + off);
+        const float4 wh = *reinterpret_cast<const float4*>(st + 2 * MT + off);
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+            const uint2 u = *reinterpret_cast<const uint2*>(xb + (warp * CPW + q) * R + off);
+            const float a0 = __uint_as_float(u.x << 16), a1 = __uint_as_float(u.x & 0xffff0000u);
+            const float a2 = __uint_as_float(u.y << 16), a3 = __uint_as_float(u.y & 0xffff0000u);
+            part[q][0] = __fmaf_rn(a0, zh.x, part[q][0]);
+            part[q][1] = __fmaf_rn(a1, zh.y, part[q][1]);
+            part[q][2] = __fmaf_rn(a2, zh.z, part[q][2]);
+            part[q][3] = __fmaf_rn(a3, zh.w, part[q][3]);
+            part2[q][0] = __fmaf_rn(a0, wh.x, part2[q][0]);
+            part2[q][1] = __fmaf_rn(a1, wh.y, part2[q][1]);
+            part2[q][2] = __fmaf_rn(a2, wh.z, part2[q][2]);
+            part2[q][3] = __fmaf_rn(a3, wh.w, part2[q][3]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+        const float sum = __fadd_rn(__fadd_rn(part[q][0], part[q][1]), __fadd_rn(part[q][2], part[q][3]));
+        ff_add(acc_s[q][0], acc_c[q][0], sum, 0.f);
+        const float sum2 = __fadd_rn(__fadd_rn(part2[q][0], part2[q][1]), __fadd_rn(part2[q][2], part2[q][3]));
+        ff_add(acc2_s[q][0], acc2_c[q][0], sum2, 0.f);
+    }
+}
+
 // Everything the end-of-group finalisation needs.
 struct FlushCtx {
     double* T;
@@ -133,8 +225,10 @@ struct FlushCtx {
     int64_t k;          // row of T being written (basis index)
     int64_t piv;        // column whose basis this is: its residual is set to 0
     double inv_nu;      // dot products were taken with v2; xi_k = v2 / nu
+    double q;           // A-norm form: xi_k' A xi_k
     uint32_t* gcnt;     // per-group arrival counters (zero at rest)
     double* gslot;      // per-group partial sums (ngroups x KMAX x C)
+    double* gslot2;     // A-norm form: the same for the dot products with z
     double* gsum;       // per-group sums of e_j
     int KMAX;
     int64_t W, NT, G, b, L0, L1;
@@ -146,14 +240,17 @@ struct FlushCtx {
 // order), publish or combine partials of a group split between CTAs (the last CTA to arrive
 // sums them in CTA order), and finalise the group's columns: T(k, j), e_j, the running argmax
 // (best_e, best_j) and the group sum of e_j.  Called by all consumer threads (NCONS).
-template <int CPW, int C, int NCONS>
-__device__ __forceinline__ void flush_group(const FlushCtx& f, int64_t g, int warp, int lane, int tid,
-                                            float (&acc_s)[CPW][4], float (&acc_c)[CPW][4],
-                                            const double (&e_old)[CPW], double& best_e, int64_t& best_j,
-                                            int& gbuf) {
+// WT (the A-norm form): the accumulators acc2 hold the dot products with z, b_j = z' x_j / nu,
+// and the indicator update of Eq. (evalerr) becomes e_j <- e_j - c_j (2 b_j - c_j q).
+template <int CPW, int C, int NCONS, bool WT>
+__device__ __forceinline__ void flush_group_t(const FlushCtx& f, int64_t g, int warp, int lane, int tid,
+                                              float (&acc_s)[CPW][4], float (&acc_c)[CPW][4],
+                                              float (&acc2_s)[CPW][4], float (&acc2_c)[CPW][4],
+                                              const double (&e_old)[CPW], double& best_e, int64_t& best_j,
+                                              int& gbuf) {
     const int64_t c0 = g * C;
     const int ncols = (int)min((int64_t)C, f.n - c0);
-    double tot[CPW];
+    double tot[CPW], tot2[CPW];
 #pragma unroll
     for (int q = 0; q < CPW; ++q) {
         float sq = acc_s[q][0], cq = acc_c[q][0];
@@ -163,6 +260,16 @@ __device__ __forceinline__ void flush_group(const FlushCtx& f, int64_t g, int wa
         tot[q] = ff_to_double(sq, cq);
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc_s[q][e] = acc_c[q][e] = 0.f;
+        tot2[q] = 0.0;
+        if constexpr (WT) {
+            float s2 = acc2_s[q][0], c2 = acc2_c[q][0];
+#pragma unroll
+            for (int e = 1; e < 4; ++e) ff_add(s2, c2, acc2_s[q][e], acc2_c[q][e]);
+            warp_sum_ff(s2, c2);
+            tot2[q] = ff_to_double(s2, c2);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc2_s[q][e] = acc2_c[q][e] = 0.f;
+        }
     }
     const bool whole = (g * f.NT >= f.L0) && ((g + 1) * f.NT <= f.L1);
     if (!whole) {
@@ -174,7 +281,10 @@ __device__ __forceinline__ void flush_group(const FlushCtx& f, int64_t g, int wa
 #pragma unroll
             for (int q = 0; q < CPW; ++q) {
                 const int cw = warp * CPW + q;
-                if (cw < ncols) f.gslot[(g * f.KMAX + slot) * C + cw] = tot[q];
+                if (cw < ncols) {
+                    f.gslot[(g * f.KMAX + slot) * C + cw] = tot[q];
+                    if constexpr (WT) f.gslot2[(g * f.KMAX + slot) * C + cw] = tot2[q];
+                }
             }
             __threadfence();
         }
@@ -191,6 +301,12 @@ __device__ __forceinline__ void flush_group(const FlushCtx& f, int64_t g, int wa
                     double acc = 0.0;
                     for (uint32_t sl = 0; sl < ncontrib; ++sl) acc += __ldcg(&f.gslot[(g * f.KMAX + sl) * C + cw]);
                     tot[q] = acc;
+                    if constexpr (WT) {
+                        double acc2 = 0.0;
+                        for (uint32_t sl = 0; sl < ncontrib; ++sl)
+                            acc2 += __ldcg(&f.gslot2[(g * f.KMAX + sl) * C + cw]);
+                        tot2[q] = acc2;
+                    }
                 }
             }
         }
@@ -204,7 +320,13 @@ __device__ __forceinline__ void flush_group(const FlushCtx& f, int64_t g, int wa
                 const int64_t j = c0 + cw;
                 const double cj = tot[q] * f.inv_nu;
                 f.T[j * f.ldt + f.k] = cj;
-                const double en = (j == f.piv) ? 0.0 : fmax(e_old[q] - cj * cj, 0.0);
+                double en;
+                if constexpr (WT) {
+                    const double bj = tot2[q] * f.inv_nu;
+                    en = (j == f.piv) ? 0.0 : fmax(e_old[q] - cj * (2.0 * bj - cj * f.q), 0.0);
+                } else {
+                    en = (j == f.piv) ? 0.0 : fmax(e_old[q] - cj * cj, 0.0);
+                }
                 f.e[j] = en;
                 f.grp_e[gbuf * C + cw] = en;
                 if (better(en, j, best_e, best_j)) {
@@ -223,6 +345,15 @@ __device__ __forceinline__ void flush_group(const FlushCtx& f, int64_t g, int wa
         f.gsum[g] = sacc;
     }
     gbuf ^= 1;
+}
+
+template <int CPW, int C, int NCONS>
+__device__ __forceinline__ void flush_group(const FlushCtx& f, int64_t g, int warp, int lane, int tid,
+                                            float (&acc_s)[CPW][4], float (&acc_c)[CPW][4],
+                                            const double (&e_old)[CPW], double& best_e, int64_t& best_j,
+                                            int& gbuf) {
+    flush_group_t<CPW, C, NCONS, false>(f, g, warp, lane, tid, acc_s, acc_c, acc_s, acc_c, e_old, best_e, best_j,
+                                        gbuf);
 }
 
 }  // namespace rbd

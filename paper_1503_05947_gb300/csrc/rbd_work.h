@@ -17,9 +17,10 @@
 //   e, xn2   running squared residuals e_j and the initial squared norms ||x_j||^2 (n each)
 //   vpart    partial sums of the row-parallel GEMVs (LC_MAX x ldp)
 //   hpart, h partial and final re-orthogonalisation coefficients (RC_MAX x d_max, d_max)
-//   nu2part  per-row-block partial squared norms (RB)
+//   nu2part  per-row-block partial squared norms (RB; 2 G on the loop path: Euclidean, A-norm)
+//   zs       loop path, A-norm form: z = (I - Y Y') (w o v2) split like v2s (the second pivot vector)
 //   rb_cnt, lb_cnt, gcnt   last-arriver counters (zero at rest)
-//   gslot    per-column-group partial dot products (ngroups x KMAX x C)
+//   gslot    per-column-group partial dot products (2 x ngroups x KMAX x C: xi, then z)
 //   gsum     per-column-group sums of e_j (ngroups)
 //   pbest_e/j  per-CTA argmax candidates of the fused pass (G)
 #pragma once
@@ -109,6 +110,14 @@ struct TileCfg<2> {
     static constexpr int PL = 1, ESIZE = 2;
 };
 
+// The diagonal A-norm form (Section 3.2) streams a second pivot-vector tile per unit: the stage
+// holds [xi hi | xi lo | z hi | z lo] (2 * MT floats each pair) ahead of the X tile.
+template <int XT>
+struct TileCfgW : TileCfg<XT> {
+    static constexpr int XI_FLOATS = 4 * TileCfg<XT>::MT;
+    static constexpr int STAGE_FLOATS = TileCfg<XT>::STAGE_FLOATS + 2 * TileCfg<XT>::MT;
+};
+
 constexpr int kGemvRows = 128;     // rows per CTA of the row-parallel GEMVs
 constexpr int kGemvTargetCtas = 304;
 constexpr int kLoopMaxRows = 512;  // largest row block per CTA of the persistent loop kernel
@@ -117,6 +126,8 @@ struct Work {
     // sizes
     int64_t m, n, ldx, ldp, d_max;
     int xt;                 // rbd_dtype
+    int wt;                 // 1: diagonal A-norm form (weights wts, loop kernel only)
+    const double* wts;      // m weights of A = diag(wts), device (caller-owned), or nullptr
     int planes_n;           // number of planes P
     int esize;              // bytes per plane element
     // pass geometry
@@ -143,6 +154,7 @@ struct Work {
     float* ysb;             // loop path: split Y, row-block-major [G_loop][2][d_max][R]
     double *v1, *v2;
     float *v1h, *v1l, *v2s;
+    float* zs;              // loop path: tile-interleaved split z of the A-norm form (as v2s)
     double *e, *xn2;
     double* vpart;
     double *hpart, *h;
@@ -159,12 +171,15 @@ struct Work {
 
 // Fill sizes/geometry of `w` (region offsets in the pointer fields); false on unsupported sizes.
 // loop_max_smem > 0 allows the persistent loop kernel with at most that much shared memory.
+// wt = 1 plans the loop kernel of the A-norm form (larger pass stages); the workspace layout
+// does not depend on wt.
 bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms,
-               int pass_ctas_per_sm, int loop_max_smem);
+               int pass_ctas_per_sm, int loop_max_smem, int wt = 0);
 // Carve the regions of `w` out of `base` (at least w.total_bytes, 256-byte aligned).
 void carve_work(Work& w, void* base);
 
 // ---- launchers (each returns the cudaError_t of its launch) ----
+// With w.wts set: e_j = ||x_j||_A^2 (xn2 stays Euclidean) and the tolerance scales in A-norms.
 cudaError_t launch_init(const Work& w, const void* X, double tol, int mode, int64_t start,
                         cudaStream_t st);
 cudaError_t launch_orth_a1(const Work& w, const void* X, const double* T, int64_t ldt, int64_t k,
@@ -188,8 +203,8 @@ cudaError_t pass_kernel_setup(int ctas_per_sm[3]);
 
 // Persistent loop kernel: shared-memory bytes for a plan (0 if the storage type has no loop
 // kernel), one-time attribute setup, and the cooperative launch of the whole greedy loop.
-size_t loop_smem_bytes(int xt, int R, int LC);
-int loop_chunk_cols_for(int xt, int R);
+size_t loop_smem_bytes(int xt, int wt, int R, int LC);
+int loop_chunk_cols_for(int xt, int wt, int R);
 cudaError_t loop_kernel_setup(int max_smem);
 cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, double* T, int64_t ldt,
                         int64_t* pivots, double* err, double* nu_out, int64_t k0, cudaStream_t st);

@@ -79,6 +79,10 @@ def load():
     lib.rbd_compress.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
                                  _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.c_size_t, _PTR,
                                  ctypes.POINTER(_Result)]
+    lib.rbd_compress_weighted.restype = ctypes.c_int
+    lib.rbd_compress_weighted.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _PTR, _DBL, ctypes.c_int, _I64, _I64,
+                                          _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.c_size_t, _PTR,
+                                          ctypes.POINTER(_Result)]
     lib.rbd_compress_host.restype = ctypes.c_int
     lib.rbd_compress_host.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
                                       _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.POINTER(_Result)]
@@ -179,8 +183,10 @@ def workspace_bytes(m: int, n: int, d_max: int, dtype=torch.float64) -> int:
 
 
 def compress(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: str = "maxcol_abs",
-             workspace: Optional[torch.Tensor] = None) -> Compressed:
-    """Algorithm 1 on a column-major CUDA tensor X (m x n) of dtype float64/float32/bfloat16."""
+             workspace: Optional[torch.Tensor] = None, weights: Optional[torch.Tensor] = None) -> Compressed:
+    """Algorithm 1 on a column-major CUDA tensor X (m x n) of dtype float64/float32/bfloat16.
+    With ``weights`` (m positive float64 values on X's device) the error is measured in the
+    A-norm of A = diag(weights) (Section 3.2; rbd_compress_weighted)."""
     lib = load()
     if not X.is_cuda:
         raise ValueError("X must be a CUDA tensor (use compress_host for host arrays)")
@@ -189,6 +195,10 @@ def compress(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: 
     m, n = X.shape
     ldx = _colmajor(X, "X")
     dev = X.device
+    if weights is not None:
+        if (not weights.is_cuda or weights.device != dev or weights.dtype != torch.float64
+                or weights.numel() != m or not weights.is_contiguous()):
+            raise ValueError("weights must be a contiguous float64 CUDA tensor of m entries on X's device")
     Y = colmajor_empty(m, d_max, torch.float64, dev)
     T = colmajor_empty(d_max, n, torch.float64, dev)
     piv = torch.empty(d_max, dtype=torch.int64, device=dev)
@@ -199,11 +209,17 @@ def compress(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: 
         ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     res = _Result()
     with torch.cuda.device(dev):
-        st = lib.rbd_compress(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, float(tol), TOL_MODES[tol_mode],
-                              int(d_max), int(start), Y.data_ptr(), m, T.data_ptr(), d_max, piv.data_ptr(),
-                              err.data_ptr(), nu.data_ptr(), ws_ptr, ws_bytes, _stream_ptr(dev),
-                              ctypes.byref(res))
-    _check(st, "rbd_compress")
+        if weights is None:
+            st = lib.rbd_compress(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, float(tol), TOL_MODES[tol_mode],
+                                  int(d_max), int(start), Y.data_ptr(), m, T.data_ptr(), d_max, piv.data_ptr(),
+                                  err.data_ptr(), nu.data_ptr(), ws_ptr, ws_bytes, _stream_ptr(dev),
+                                  ctypes.byref(res))
+        else:
+            st = lib.rbd_compress_weighted(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, weights.data_ptr(), float(tol),
+                                           TOL_MODES[tol_mode], int(d_max), int(start), Y.data_ptr(), m,
+                                           T.data_ptr(), d_max, piv.data_ptr(), err.data_ptr(), nu.data_ptr(),
+                                           ws_ptr, ws_bytes, _stream_ptr(dev), ctypes.byref(res))
+    _check(st, "rbd_compress" if weights is None else "rbd_compress_weighted")
     d = int(res.d)
     return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
                       STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),

@@ -28,7 +28,7 @@ def lib():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for f in ("rbd_compress", "rbd_compress_host", "rbd_project", "rbd_compress_workspace_bytes",
+    for f in ("rbd_compress", "rbd_compress_host", "rbd_compress_weighted", "rbd_project", "rbd_compress_workspace_bytes",
               "rbd_status_string", "rbd_version", "rbd_set_profiling", "rbd_get_profile"):
         assert f in names, f
 
@@ -84,6 +84,17 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     assert call(mode=3) == 1
     assert call(xt=7) == 1
     assert call(ldt=3) == 1
+    # the A-norm form: the same checks, plus a NULL or misaligned weight vector
+    def wcall(w, **kw):
+        a = dict(X=P, m=8, n=6, ldx=8, d_max=4)
+        a.update(kw)
+        return lib.rbd_compress_weighted(a["X"], 0, a["m"], a["n"], a["ldx"], w, 0.0, 0, a["d_max"], 0, P, 8, P, 4,
+                                         P, P, None, None, 0, None, ctypes.byref(res))
+
+    assert wcall(None) == 1
+    assert wcall(ctypes.c_void_p(20)) == 1   # not 8-byte aligned
+    assert wcall(P, X=None) == 1
+    assert wcall(P, d_max=9) == 1
     assert lib.rbd_project(P, 0, 2, 1, P, 0, 1, 1, P, 2, None) == 1
     assert lib.rbd_project(P, 4, 2, 3, P, 0, 1, 4, P, 2, None) == 1   # ldy < m
     assert lib.rbd_project(P, 4, 0, 4, P, 0, 1, 4, P, 1, None) == 0   # d = 0: no-op
