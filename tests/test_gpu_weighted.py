@@ -88,7 +88,7 @@ def test_weighted_matches_oracle(rbd, oracle_mod, case, dtype):
 
 
 @pytest.mark.parametrize("pin", pins.W_PINS, ids=lambda p: p.__name__)
-def test_weighted_pins_on_cuda_path(pin):
+def test_weighted_pins_on_cuda_path(rbd, pin):
     pin(gpu_compress)
 
 
