@@ -313,6 +313,7 @@ def run_gpu(args, world, rank, local):
     forms = {}
     if rank == 0 and not args.no_forms:
         forms["decode"] = decode_form(r, dev)
+        forms["weighted"] = weighted_form(X, ws, dev, (loop_ms / loop_passes) if loop_passes else None)
         forms["precision"] = precision_forms(dev)
         forms["batched"] = batched_forms(dev)
 
@@ -364,6 +365,38 @@ def decode_form(r, dev) -> dict:
     return {"workload": f"Xr = Y T, {m} x {d} times {d} x {n} (the benchmark's compression)", "ms": ms,
             "fma_per_s": m * n * d / (ms * 1e-3), "out_gbs": m * n * 8 / (ms * 1e-3) / 1e9,
             "arith": "float-float products on the FP32 pipes (FP64-grade)"}
+
+
+def weighted_form(X, ws, dev, plain_pass_ms) -> dict:
+    """The diagonal A-norm form (Section 3.2): the benchmark's matrix and tolerance with row
+    weights (gen.row_weights, seed 7: a smooth bump up to 10x over a third of the rows times a
+    0.5-2x jitter), CUDA events around one rbd_compress_weighted call after a warm-up call, and
+    the persistent kernel's time per pass against the unweighted run's."""
+    import torch
+
+    import gen
+    import paper_1503_05947_gb300 as rbd
+    w = torch.as_tensor(gen.row_weights(M, seed=7), device=dev)
+    rbd.compress(X, TOL, D_MAX, tol_mode=TOL_MODE, workspace=ws, weights=w)
+    rbd.set_profiling(True)
+    stream = torch.cuda.current_stream(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    r = rbd.compress(X, TOL, D_MAX, tol_mode=TOL_MODE, workspace=ws, weights=w)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    pf = rbd.get_profile()
+    rbd.set_profiling(False)
+    ms = ev0.elapsed_time(ev1)
+    pass_ms = pf["loop_ms"] / max(r.d, 1)
+    out = {"workload": f"A = diag(w) on the benchmark matrix ({M}x{N} FP64, d_max {D_MAX}, {TOL_MODE} {TOL})",
+           "ms": ms, "bases": r.d, "stop_reason": r.stop_reason, "fro_rel_residual_A": r.fro_last / r.x_fro,
+           "gbs": r.d * M * N * 8 / (pf["loop_ms"] * 1e-3) / 1e9, "pass_ms": pass_ms}
+    if plain_pass_ms:
+        out["pass_time_vs_unweighted"] = pass_ms / plain_pass_ms
+    return out
 
 
 PREC_M, PREC_N, PREC_DMAX = 65536, 16384, 256
