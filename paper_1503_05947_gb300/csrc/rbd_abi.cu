@@ -62,12 +62,14 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
         const int64_t gl = std::min<int64_t>(num_sms, std::max<int64_t>(w.W, ceil_div(w.ldp, kLoopMaxRows)));
         const int64_t R = round_up(ceil_div(w.ldp, gl), 4);
         if (R <= kLoopMaxRows) {
-            const int LC = loop_chunk_cols_for(xt, wt, (int)R);
+            const int64_t RS = (R % 8 == 4) ? R : R + 4;
+            const int LC = loop_chunk_cols_for(xt, wt, (int)RS);
             const size_t smem = loop_smem_bytes(xt, wt, (int)R, LC);
             if (LC >= 4 && smem > 0 && smem <= (size_t)loop_max_smem) {
                 w.use_loop = 1;
                 w.G_loop = (int)gl;
                 w.R = (int)R;
+                w.RS = (int)RS;
                 w.LC = LC;
                 w.loop_smem = smem;
             }
@@ -107,7 +109,7 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     size_t o_planes = take((size_t)w.ngroups * (size_t)w.group_stride * w.esize);
     size_t o_yh = take(lp ? 0 : ldp * (size_t)d_max * 4);
     size_t o_yl = take(lp ? 0 : ldp * (size_t)d_max * 4);
-    size_t o_ysb = take(lp ? (size_t)w.G_loop * 2 * (size_t)d_max * (size_t)w.R * 4 : 0);
+    size_t o_ysb = take(lp ? (size_t)w.G_loop * 2 * (size_t)d_max * (size_t)w.RS * 4 : 0);
     size_t o_v1 = take(lp ? 0 : ldp * 8), o_v2 = take(lp ? 0 : ldp * 8);
     size_t o_v1h = take(lp ? 0 : ldp * 4), o_v1l = take(lp ? 0 : ldp * 4);
     size_t o_v2s = take((size_t)w.NT * 2 * w.MT * 4);

@@ -117,6 +117,27 @@ __device__ __forceinline__ void ff_add(float& s, float& c, float s2, float c2) {
     c = __fadd_rn(c, __fadd_rn(c2, e));
 }
 
+// s + e == a + b exactly, for |a| >= |b| or a == 0 (Fast2Sum).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (s, c) += (s2, c2) with the error bounded relative to the SUM (the accurate double-word addition
+// of Joldes, Muller and Popescu, "Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic", ACM TOMS 2017): both parts are added with TwoSum and the result is
+// renormalised twice.  ff_add bounds its error by the larger operand instead, which is too coarse
+// when partial sums cancel.
+__device__ __forceinline__ void ff_add_acc(float& s, float& c, float s2, float c2) {
+    float sh, sl, th, tl;
+    two_sum(s, s2, sh, sl);
+    two_sum(c, c2, th, tl);
+    sl = __fadd_rn(sl, th);
+    fast_two_sum(sh, sl, sh, sl);
+    sl = __fadd_rn(sl, tl);
+    fast_two_sum(sh, sl, s, c);
+}
+
 // Float-float sum over the 32 lanes of a warp (fixed tree); the result is valid in lane 0.
 __device__ __forceinline__ void warp_sum_ff(float& s, float& c) {
 #pragma unroll

@@ -68,7 +68,7 @@ struct LoopParams {
     uint32_t* bar;        // grid barrier {count, generation}
     double* e;
     const double* xn2;
-    float* ysb;           // [G][2][d_max][R] split Y, row-block-major
+    float* ysb;           // [G][2][d_max][RS] split Y, row-block-major
     float* v2s;           // tile-interleaved split v2 (pivot-vector tiles of the pass)
     float* zs;            // A-norm form: tile-interleaved split z (second pivot vector)
     double* hpart;        // [G][d_max]
@@ -81,6 +81,7 @@ struct LoopParams {
     double* gslot2;       // A-norm form: group partials of the dot products with z
     double* gsum;
     int R;                // rows per CTA block (multiple of 4, <= kLoopMaxRows)
+    int RS;               // column stride of a Y slice (R or R + 4, RS = 4 mod 8: see loop_slice_stride)
     int LC;               // Y columns per streamed chunk (multiple of 4)
 };
 
@@ -118,12 +119,13 @@ __host__ __device__ inline LoopSmem loop_smem_layout(int R, int LC) {
     size_t o = (size_t)Cfg::S * Cfg::STAGE_FLOATS * 4;  // the ring: pass stages / Y chunks
     s.bars = o;
     o += (size_t)(3 * Cfg::S) * 8;                // full, empty, ybar
+    o = (o + 15) & ~size_t(15);                   // 16-byte loads from the regions below
     s.v1s = o;
     o += (size_t)R * 8;
     s.v2own = o;
     o += (size_t)R * 8;
     s.part = o;
-    o += (size_t)(R > 256 ? R : 256) * 8;
+    o += (size_t)8 * (Cfg::NW * 32) * 4;          // partial sums of the slice GEMVs (8 NCONS floats)
     s.coef = o;
     o += (size_t)Cfg::S * 2 * LC * 4;             // per ring buffer: (hi, lo) x LC
     s.v1split = o;
@@ -179,7 +181,7 @@ struct YStream {
     float* coef;        // NB x 2 x LC
     const float* ysb_b; // this CTA's block of the split Y
     int64_t d_max;
-    int R, LC;
+    int R, LC;          // R: column stride of the slice (floats)
     uint64_t pol;
     uint32_t count;     // chunks streamed so far (all calls): fixes each chunk's buffer and parity
     bool loaded;        // the slice of this step is resident in the ring
@@ -217,6 +219,9 @@ __device__ __forceinline__ void ystream(YStream& ys, int64_t k, int np, int tid,
     };
     // Resident mode: when the whole slice fits in the ring (nch <= NB) it is loaded by the first
     // call of a step and reused by the later calls of the same step (ystream_end_step releases it).
+    // A resident slice is never overwritten within the step and all its coefficients are staged
+    // up front, so one barrier before the first chunk suffices; a streamed slice recycles its
+    // buffers and synchronises per chunk.
     const bool resident = nch <= ys.NB;
     const bool reuse = resident && ys.loaded;
     const int64_t npre = min(nch, (int64_t)ys.NB);
@@ -224,7 +229,8 @@ __device__ __forceinline__ void ystream(YStream& ys, int64_t k, int np, int tid,
         for (int64_t c = 0; c < npre; ++c) issue(c);
     for (int64_t c = 0; c < npre; ++c) stage_coef(c);
     for (int64_t c = 0; c < nch; ++c) {
-        named_bar(1, NCONS);  // coefficients visible; chunk c-1 consumed, so its buffer is free
+        if (!resident || c == 0)
+            named_bar(1, NCONS);  // coefficients visible; chunk c-1 consumed, so its buffer is free
         if (!resident && c >= 1 && c - 1 + ys.NB < nch) {
             if (tid == 0) issue(c - 1 + ys.NB);
             stage_coef(c - 1 + ys.NB);
@@ -294,7 +300,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     Ctl* ctl = p.ctl;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t G = gridDim.x, b = blockIdx.x;
-    const int R = p.R;
+    const int R = p.R, RS = p.RS;
     const int64_t r0 = b * (int64_t)R;
     const int Rb = (int)max((int64_t)0, min((int64_t)R, p.ldp - r0));  // rows of this block within ldp
     const int64_t W = p.W, NT = p.NT;
@@ -317,13 +323,13 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     uint32_t gen = 0;
     YStream ys;
     ys.ring = stages;
-    ys.buf_floats = loop_ybuf_stages<Cfg>(R) * STAGE;
-    ys.NB = S / loop_ybuf_stages<Cfg>(R);
+    ys.buf_floats = loop_ybuf_stages<Cfg>(RS) * STAGE;
+    ys.NB = S / loop_ybuf_stages<Cfg>(RS);
     ys.ybar = ybar;
     ys.coef = coef;
-    ys.ysb_b = p.ysb + b * 2 * p.d_max * (int64_t)R;
+    ys.ysb_b = p.ysb + b * 2 * p.d_max * (int64_t)RS;
     ys.d_max = p.d_max;
-    ys.R = R;
+    ys.R = RS;
     ys.LC = p.LC;
     ys.pol = l2_policy_evict_normal();
     ys.count = 0;
@@ -342,7 +348,6 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     uint32_t pf_ph0 = 0;
 
     int64_t piv = ctl->pivot;
-    double fro_prev = ctl->fro_last;
     const int mode = ctl->mode;
     const double eps_r = ctl->eps_r, eps_r22 = ctl->eps_r22, fro_tol = ctl->fro_tol;
     const unsigned char* planes = p.planes;
@@ -353,48 +358,108 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     int32_t stop = STOP_NONE;
     double nu = 0.0;
     for (;; ++k) {
+
+        // Rows in quads of 4 for the column dots (Rb is a multiple of 4): 16-byte shared-memory
+        // loads, four float-float chains per thread, and with the slice stride RS = 4 mod 8 (RS / 4
+        // odd) the 8 threads of a quarter-warp that read 8 consecutive columns of one quad hit 8
+        // different 16-byte bank groups.
+        const int NQ = Rb / 4;
+
+        // GEMV over the slice: S_r = sum_{l<k} Y_b(r, l) coef(l) for this block's rows.  Thread
+        // (rfirst, q) sums row rfirst over the columns l = q, q + NSUB, ... of each chunk in two
+        // alternating float-float chains; the NSUB column subsets are added in FP64 in subset
+        // order (v = x - S cancels heavily when the pivot nearly lies in span(Y), so S needs more
+        // than a float-float combine of many partial sums).  fin(r, i, S_r) runs for every r < R
+        // in thread r - i * NCONS = tid (S_r = 0 for rows >= Rb).  Consumers only.
         const int NSUB = (R <= NCONS) ? (NCONS / R) : 1;
         const int q = (R <= NCONS) ? (tid / R) : 0;
         const int rfirst = (R <= NCONS) ? (tid % R) : tid;
         const bool active = (warp < NW) && ((R <= NCONS) ? (tid < NSUB * R) : true);
+        auto block_gemv = [&](auto&& load_coef, auto&& fin) {
+            float as[MAXRPT], ac[MAXRPT], bs[MAXRPT], bc[MAXRPT];
+#pragma unroll
+            for (int i = 0; i < MAXRPT; ++i) as[i] = ac[i] = bs[i] = bc[i] = 0.f;
+            if (k > 0) {
+                ystream<NCONS>(ys, k, 2, tid, ctl, load_coef,
+                               [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
+                                   if (!active) return;
+#pragma unroll
+                                   for (int i = 0; i < MAXRPT; ++i) {
+                                       const int r = rfirst + i * NCONS;
+                                       if (r >= Rb || (R <= NCONS && i > 0)) break;
+                                       int l = q;
+                                       for (; l + NSUB < lc; l += 2 * NSUB) {
+                                           ff_mac2(as[i], ac[i], yh[l * RS + r], yl[l * RS + r], ch[l], cl[l]);
+                                           ff_mac2(bs[i], bc[i], yh[(l + NSUB) * RS + r], yl[(l + NSUB) * RS + r],
+                                                   ch[l + NSUB], cl[l + NSUB]);
+                                       }
+                                       if (l < lc) ff_mac2(as[i], ac[i], yh[l * RS + r], yl[l * RS + r], ch[l], cl[l]);
+                                   }
+                               });
+            }
+#pragma unroll
+            for (int i = 0; i < MAXRPT; ++i) ff_add(as[i], ac[i], bs[i], bc[i]);
+            if (R <= NCONS) {
+                if (active) part[q * R + rfirst] = ff_to_double(as[0], ac[0]);
+                named_bar(1, NCONS);
+                if (tid < R) {
+                    double acc = 0.0;
+                    if (tid < Rb && k > 0)
+                        for (int qq = 0; qq < NSUB; ++qq) acc += part[qq * R + tid];
+                    fin(tid, 0, acc);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < MAXRPT; ++i) {
+                    const int r = tid + i * NCONS;
+                    if (r >= R) break;
+                    fin(r, i, (r < Rb && k > 0) ? ff_to_double(as[i], ac[i]) : 0.0);
+                }
+            }
+            named_bar(1, NCONS);
+        };
 
         // out[b][l] = Y_b(:, l)' s_b for l < k, s_b = (v1h, v1l) of this block's rows (consumers).
-        // tpc consecutive threads share a column, each summing every tpc-th row in two interleaved
-        // chains; the parts are combined in float-float inside the group of lanes.  tpc (a power
-        // of two <= 32) minimises rounds x (rows per thread + combine steps).
+        // One thread per (column, row segment): the chunk's lc columns times nseg = NCONS / lc
+        // segments of the block's quads, combined in segment order through shared memory.
         auto block_dots = [&](double* out) {
             ystream<NCONS>(
                 ys, k, 2, tid, ctl, [&](int64_t, float& hi, float& lo) { hi = lo = 0.f; },
                 [&](const float* yh, const float* yl, const float*, const float*, int64_t l0, int lc) {
-                    int tpc = 1, best = 1 << 30;
-                    for (int tq = 1, lg = 0; tq <= 32; tq <<= 1, ++lg) {
-                        const int cost = ((lc + NCONS / tq - 1) / (NCONS / tq)) * ((Rb + tq - 1) / tq + 2 * lg);
-                        if (cost < best) {
-                            best = cost;
-                            tpc = tq;
+                    const int nseg = max(1, min(8, NCONS / lc));
+                    const int sq = (NQ + nseg - 1) / nseg;
+                    // 2 x nseg x lc <= 2 NCONS floats per chunk, double-buffered by chunk parity: the
+                    // one barrier per chunk below then also orders the reads of chunk c before the
+                    // writes of chunk c + 2
+                    float* pf = reinterpret_cast<float*>(part) + (((l0 / ys.LC) & 1) ? 2 * NCONS : 0);
+                    if (tid < nseg * lc) {
+                        const int l = tid % lc, sg = tid / lc;
+                        const int q0 = sg * sq, q1 = min(NQ, q0 + sq);
+                        const float* ch = yh + l * RS;
+                        const float* cl = yl + l * RS;
+                        float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
+                        for (int qq = q0; qq < q1; ++qq) {
+                            const float4 a = *reinterpret_cast<const float4*>(ch + 4 * qq);
+                            const float4 al = *reinterpret_cast<const float4*>(cl + 4 * qq);
+                            const float4 v = *reinterpret_cast<const float4*>(v1h + 4 * qq);
+                            const float4 vl = *reinterpret_cast<const float4*>(v1l + 4 * qq);
+                            ff_mac2(s4[0], c4[0], a.x, al.x, v.x, vl.x);
+                            ff_mac2(s4[1], c4[1], a.y, al.y, v.y, vl.y);
+                            ff_mac2(s4[2], c4[2], a.z, al.z, v.z, vl.z);
+                            ff_mac2(s4[3], c4[3], a.w, al.w, v.w, vl.w);
                         }
+                        ff_add_acc(s4[0], c4[0], s4[1], c4[1]);
+                        ff_add_acc(s4[2], c4[2], s4[3], c4[3]);
+                        ff_add_acc(s4[0], c4[0], s4[2], c4[2]);
+                        pf[2 * (sg * lc + l)] = s4[0];
+                        pf[2 * (sg * lc + l) + 1] = c4[0];
                     }
-                    const int per = NCONS / tpc;
-                    for (int lb = 0; lb < lc; lb += per) {
-                        const int l = lb + tid / tpc, qq = tid % tpc;
-                        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
-                        if (l < lc) {
-                            const float* ch = yh + l * R;
-                            const float* cl = yl + l * R;
-                            int r = qq;
-                            for (; r + tpc < Rb; r += 2 * tpc) {
-                                ff_mac2(s0, c0, ch[r], cl[r], v1h[r], v1l[r]);
-                                ff_mac2(s1, c1, ch[r + tpc], cl[r + tpc], v1h[r + tpc], v1l[r + tpc]);
-                            }
-                            if (r < Rb) ff_mac2(s0, c0, ch[r], cl[r], v1h[r], v1l[r]);
-                            ff_add(s0, c0, s1, c1);
-                        }
-                        for (int o = 1; o < tpc; o <<= 1) {
-                            const float s2 = __shfl_xor_sync(0xffffffffu, s0, o);
-                            const float c2 = __shfl_xor_sync(0xffffffffu, c0, o);
-                            ff_add(s0, c0, s2, c2);
-                        }
-                        if (l < lc && qq == 0) out[b * p.d_max + l0 + l] = ff_to_double(s0, c0);
+                    named_bar(1, NCONS);
+                    if (tid < lc) {
+                        float s0 = pf[2 * tid], c0 = pf[2 * tid + 1];
+                        for (int sg = 1; sg < nseg; ++sg)
+                            ff_add_acc(s0, c0, pf[2 * (sg * lc + tid)], pf[2 * (sg * lc + tid) + 1]);
+                        out[b * p.d_max + l0 + tid] = ff_to_double(s0, c0);
                     }
                 });
         };
@@ -402,41 +467,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
         // v1s).  Float-float: when the pivot nearly lies in span(Y), v1 is tiny and the coefficients
         // are not small relative to it, so Y h needs the full precision for Y'Y = I to hold.
         auto block_sub = [&](const double* coefv, double* dst) {
-            float as[MAXRPT], ac[MAXRPT];
-#pragma unroll
-            for (int i = 0; i < MAXRPT; ++i) as[i] = ac[i] = 0.f;
-            if (k > 0) {
-                ystream<NCONS>(
-                    ys, k, 2, tid, ctl,
-                    [&](int64_t l, float& hi, float& lo) { split_double(__ldcg(&coefv[l]), hi, lo); },
-                    [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
-                        if (!active) return;
-#pragma unroll
-                        for (int i = 0; i < MAXRPT; ++i) {
-                            const int r = rfirst + i * NCONS;
-                            if (r >= Rb || (R <= NCONS && i > 0)) break;
-                            for (int l = q; l < lc; l += NSUB)
-                                ff_mac2(as[i], ac[i], yh[l * R + r], yl[l * R + r], ch[l], cl[l]);
-                        }
-                    });
-            }
-            if (R <= NCONS) {
-                if (active) part[q * R + rfirst] = ff_to_double(as[0], ac[0]);
-                named_bar(1, NCONS);
-                for (int r = tid; r < R; r += NCONS) {
-                    double corr = 0.0;
-                    for (int qq = 0; qq < NSUB; ++qq) corr += part[qq * R + r];
-                    dst[r] = (r < Rb) ? v1s[r] - corr : 0.0;
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < MAXRPT; ++i) {
-                    const int r = rfirst + i * NCONS;
-                    if (r >= R) break;
-                    dst[r] = (r < Rb) ? v1s[r] - ff_to_double(as[i], ac[i]) : 0.0;
-                }
-            }
-            named_bar(1, NCONS);
+            block_gemv([&](int64_t l, float& hi, float& lo) { split_double(__ldcg(&coefv[l]), hi, lo); },
+                       [&](int r, int, double sv) { dst[r] = (r < Rb) ? v1s[r] - sv : 0.0; });
         };
         // split copy of this block's rows of src for the pass: tile t of dstv holds
         // [hi(rows_t) | lo(rows_t)] at t * 2 * MT (consumers).
@@ -488,56 +520,32 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
 
         // ---------------- O1 / O1': v1 = x_i - Y t, partial h = Y_b' v1_b ----------------
         if (warp < NW) {
-            // the pivot column's rows of this block, loaded now so the loads overlap the stream
-            // (v2own is free until O3; each thread later reads back only the rows it loaded)
-            for (int r = tid; r < R; r += NCONS)
-                v2own[r] = (r < Rb && r0 + r < p.m) ? load_x_elem(p.X, p.xt, piv * p.ldx + r0 + r) : 0.0;
-            float as[MAXRPT], ac[MAXRPT];
+            // the pivot column's rows of this block (row tid + i NCONS in thread tid), held in
+            // registers so that the loads overlap the coefficient loads and the stream
+            double xr[MAXRPT];
 #pragma unroll
-            for (int i = 0; i < MAXRPT; ++i) as[i] = ac[i] = 0.f;
-            if (k > 0) {
-                const double* tcol = p.T + piv * p.ldt;
-                ystream<NCONS>(
-                    ys, k, 2, tid, ctl,
-                    [&](int64_t l, float& hi, float& lo) { split_double(__ldcg(&tcol[l]), hi, lo); },
-                    [&](const float* yh, const float* yl, const float* ch, const float* cl, int64_t, int lc) {
-                        if (!active) return;
-#pragma unroll
-                        for (int i = 0; i < MAXRPT; ++i) {
-                            const int r = rfirst + i * NCONS;
-                            if (r >= Rb || (R <= NCONS && i > 0)) break;
-                            for (int l = q; l < lc; l += NSUB)
-                                ff_mac2(as[i], ac[i], yh[l * R + r], yl[l * R + r], ch[l], cl[l]);
-                        }
-                    });
+            for (int i = 0; i < MAXRPT; ++i) {
+                const int r = tid + i * NCONS;
+                xr[i] = (r < Rb && r0 + r < p.m) ? load_x_elem(p.X, p.xt, piv * p.ldx + r0 + r) : 0.0;
             }
-            // combine the column subsets and finish v1 for this block's rows
-            if (R <= NCONS) {
-                if (active) part[q * R + rfirst] = ff_to_double(as[0], ac[0]);
-                named_bar(1, NCONS);
-                for (int r = tid; r < R; r += NCONS) {
-                    double v = 0.0;
-                    if (r < Rb && r0 + r < p.m) {
-                        double acc = 0.0;
-                        for (int qq = 0; qq < NSUB; ++qq) acc += part[qq * R + r];
-                        v = v2own[r] - acc;
-                    }
-                    v1s[r] = v;
-                    split_double(v, v1h[r], v1l[r]);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < MAXRPT; ++i) {
-                    const int r = rfirst + i * NCONS;
-                    if (r >= R) break;
-                    double v = 0.0;
-                    if (r < Rb && r0 + r < p.m) v = v2own[r] - ff_to_double(as[i], ac[i]);
-                    v1s[r] = v;
-                    split_double(v, v1h[r], v1l[r]);
-                }
-            }
-            named_bar(1, NCONS);
+            const double* tcol = p.T + piv * p.ldt;
+            block_gemv([&](int64_t l, float& hi, float& lo) { split_double(__ldcg(&tcol[l]), hi, lo); },
+                       [&](int r, int i, double sv) {
+                           const double v = (r < Rb && r0 + r < p.m) ? xr[i] - sv : 0.0;
+                           v1s[r] = v;
+                           split_double(v, v1h[r], v1l[r]);
+                       });
             if (k > 0) block_dots(p.hpart);
+        }
+        if (k > 0 && b == 0 && warp == NW) {
+            // Frobenius residual after basis k-1 (fixed order), off the critical path: the pass
+            // wrote the per-group sums before barrier 4 of the last step; phase D reads it after
+            // barrier 3 of this one
+            double fs = 0.0;
+#pragma unroll 8
+            for (int64_t gg = lane; gg < p.ngroups; gg += 32) fs += __ldcg(&p.gsum[gg]);
+            fs = warp_sum_double(fs);
+            if (lane == 0) ctl->fro_last = sqrt(fmax(fs, 0.0));
         }
         if (k > 0) {
             if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;   // barrier 1
@@ -677,8 +685,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             if (r0 + r < p.m) p.Y[(r0 + r) + k * p.ldy] = y;
             float hi, lo;
             split_double(y, hi, lo);
-            p.ysb[(b * 2 + 0) * p.d_max * R + k * R + r] = hi;
-            p.ysb[(b * 2 + 1) * p.d_max * R + k * R + r] = lo;
+            p.ysb[(b * 2 + 0) * p.d_max * RS + k * RS + r] = hi;
+            p.ysb[(b * 2 + 1) * p.d_max * RS + k * RS + r] = lo;
         }
         fence_proxy_async_global();  // this block of Y is streamed by bulk copies in later steps
         if (warp == NW) {
@@ -874,27 +882,16 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                     bj = oj;
                 }
             }
-            // Frobenius residual (fixed order): CTA 0 only; it publishes it in the control block,
-            // where the other CTAs read it in the next step's phase D
-            double fs = 0.0;
-            if (b == 0) {
-#pragma unroll 8
-                for (int64_t gg = lane; gg < p.ngroups; gg += 32) fs += __ldcg(&p.gsum[gg]);
-                fs = warp_sum_double(fs);
-            }
             if (lane == 0) {
-                bcast[1] = sqrt(fmax(fs, 0.0));
                 bcast[2] = sqrt(fmax(be, 0.0));
                 red_j[0] = (bj >= 0 && bj < p.n) ? bj : piv;
             }
         }
         __syncthreads();
-        if (b == 0) fro_prev = bcast[1];
         piv = red_j[0];
         if (b == 0 && tid == 0) {
             ctl->d = k + 1;
             ctl->pivot = piv;
-            ctl->fro_last = fro_prev;
             ctl->err_downdate = bcast[2];
         }
         __syncthreads();
@@ -921,7 +918,6 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             ctl->stop = stop;
             ctl->d = k;
             ctl->pivot = piv;
-            ctl->fro_last = fro_prev;
         }
     }
 }
@@ -999,6 +995,7 @@ cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, do
     p.gslot2 = w.gslot + (size_t)w.ngroups * (size_t)w.KMAX * (size_t)w.C;
     p.gsum = w.gsum;
     p.R = w.R;
+    p.RS = w.RS;
     p.LC = w.LC;
     void* args[] = {&p};
     if (w.wt && !w.wts) return cudaErrorInvalidValue;

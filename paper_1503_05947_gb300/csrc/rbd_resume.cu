@@ -30,8 +30,8 @@ struct ResumeParams {
     const double* xn2;
     double* gsum;
     int use_loop;
-    float* ysb;   // persistent kernel: [G][2][d_max][R]
-    int R, G_loop;
+    float* ysb;   // persistent kernel: [G][2][d_max][RS]
+    int R, RS, G_loop;
     float *yh, *yl;  // stepwise path: ldp x d_max each
     int64_t d_max;
     Ctl* ctl;
@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(256) resume_y_kernel(ResumeParams p) {
             const double y = (row < p.m) ? p.Y[row + l * p.ldy] : 0.0;
             float hi, lo;
             split_double(y, hi, lo);
-            p.ysb[(b * 2 + 0) * p.d_max * p.R + l * p.R + r] = hi;
-            p.ysb[(b * 2 + 1) * p.d_max * p.R + l * p.R + r] = lo;
+            p.ysb[(b * 2 + 0) * p.d_max * p.RS + l * p.RS + r] = hi;
+            p.ysb[(b * 2 + 1) * p.d_max * p.RS + l * p.RS + r] = lo;
         }
     } else {
         const int64_t total = p.ldp * p.k0;
@@ -127,6 +127,7 @@ cudaError_t launch_resume(const Work& w, const double* Y, int64_t ldy, const dou
     p.use_loop = w.use_loop;
     p.ysb = w.ysb;
     p.R = w.R;
+    p.RS = w.RS;
     p.G_loop = w.G_loop;
     p.yh = w.yh;
     p.yl = w.yl;

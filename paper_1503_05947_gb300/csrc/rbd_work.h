@@ -11,6 +11,8 @@
 //            Element (row R, column J, plane p), g = J / C, c = J % C, t = R / MT, r = R % MT:
 //                g * C * P * ldp  +  t * C * P * MT  +  (c * P + p) * rows_t  +  r
 //   yh, yl   split FP32 copy of Y (ldp x d_max each), read by the orthogonalisation GEMVs
+//   ysb      loop path: split FP32 copy of Y by row block, [G][2][d_max][RS] (RS >= R rows; the
+//            stride keeps the column-parallel dot products free of shared-memory bank conflicts)
 //   v1, v2   FP64 work vectors of the current step (ldp) and split copies:
 //            v1h/v1l plain (ldp each); v2s tile-interleaved for the pass: tile t holds
 //            [hi(rows_t) | lo(rows_t)] at offset t * 2 * MT.
@@ -145,6 +147,7 @@ struct Work {
     int use_loop;
     int G_loop;             // CTAs (one per SM at most)
     int R;                  // rows per CTA block (multiple of 4)
+    int RS;                 // column stride of a CTA's Y slice: R, or R + 4, so that RS = 4 mod 8
     int LC;                 // Y columns per streamed chunk
     size_t loop_smem;       // dynamic shared memory bytes
     // regions
