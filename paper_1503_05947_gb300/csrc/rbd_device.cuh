@@ -244,6 +244,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Bulk prefetch of [src, src + bytes) into L2, untracked; src 16-byte aligned, bytes a multiple
+// of 16, the range inside one allocation.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Orders this thread's generic-proxy global writes before later async-proxy (bulk copy) reads
 // of the same data.
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -253,6 +259,11 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 // Named barrier over `nthreads` threads (a multiple of 32) with id `id` (1..15).
 __device__ __forceinline__ void named_bar(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Arrive at named barrier `id` without waiting (the waiting side calls named_bar).
+__device__ __forceinline__ void named_bar_arrive(int id, int nthreads) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 __device__ __forceinline__ void raise_status(Ctl* ctl, int32_t st) {

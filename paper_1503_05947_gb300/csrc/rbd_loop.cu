@@ -485,8 +485,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             }
             fence_proxy_async_global();  // read by bulk copies in the pass
         };
-        // producer: the X tiles of pass k (the ring is free once every consumer is done with Y);
-        // X never changes, so its first tiles load while the CTAs synchronise.
+        // producer: the first X tiles of pass k into the ring (free once every consumer is done
+        // with Y), ahead of the pivot-vector tiles.
         auto prefetch_x = [&]() {
             if (warp != NW || lane != 0 || k >= p.d_max || !ok) return;
             npref = min(nunits, (int64_t)S);
@@ -535,7 +535,26 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                            v1s[r] = v;
                            split_double(v, v1h[r], v1l[r]);
                        });
+            named_bar_arrive(2, NCONS + 32);  // O1's loads are done
             if (k > 0) block_dots(p.hpart);
+        } else {
+            // The first tiles of pass k, into L2 once O1's loads are done, while HBM is otherwise
+            // idle during the orthogonalisation; the bulk copies into shared memory before
+            // barrier 3 then hit L2 and leave HBM quiet while the CTAs synchronise.
+            named_bar(2, NCONS + 32);
+            if (lane == 0 && k < p.d_max) {
+                int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
+                const int64_t npf = min(nunits, (int64_t)S);
+                for (int64_t i = 0; i < npf; ++i) {
+                    const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                    bulk_prefetch_l2(planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE,
+                                     (uint32_t)(C * UB) * rows);
+                    if (++t == NT) {
+                        t = 0;
+                        ++g;
+                    }
+                }
+            }
         }
         if (k > 0 && b == 0 && warp == NW) {
             // Frobenius residual after basis k-1 (fixed order), off the critical path: the pass
@@ -594,13 +613,14 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 if (k > 0) block_dots(p.hpart);
             }
         }
-        if constexpr (!WT) {
-            ystream_end_step(ys);
-            __syncthreads();
-            prefetch_x();
-        }
         if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 3
         if (!ok || __ldcg(&ctl->status) != 0) break;
+        if constexpr (!WT) {
+            // every consumer is past O3, so the ring is free: the first X tiles of the pass (L2
+            // hits) load during the stop decision
+            ystream_end_step(ys);
+            prefetch_x();
+        }
 
         // ---------------- D: nu, certified E_cur of basis k-1, stop tests ----------------
         // A-norm form: E_cur and the tests of steps 2.2 / 2.4 take ||v2||_A; xi = v2 / nu and the
