@@ -33,8 +33,9 @@
 // This is classical Gram-Schmidt applied twice (see rbd_orth.cu for why, and for its accuracy);
 // Y is kept as a split FP32 copy stored ROW-BLOCK-MAJOR (block b = this CTA's R rows, all
 // columns contiguous), so each CTA streams only its own slice of Y, with bulk copies, and no
-// other CTA ever reads it.  X never changes, so the producer prefetches the first tiles of the
-// next pass while the orthogonalisation runs; only the pivot-vector tiles wait for O3.
+// other CTA ever reads it.  X never changes: the producer prefetches the first tiles of the next
+// pass into L2 while the orthogonalisation runs and into shared memory after barrier 3; only the
+// pivot-vector tiles wait for O3.
 #include <algorithm>
 #include <type_traits>
 
@@ -142,26 +143,42 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
     return v;
 }
 
+// Bit 31 of the grid-barrier word: set by a CTA that raised an error, so that every other CTA
+// leaves at its next barrier without a separate read of the status word (the arrival count stays
+// far below 2^31: G * 4 barriers per basis).
+constexpr uint32_t kAbortBit = 0x80000000u;
+
+__device__ __forceinline__ void loop_abort(Ctl* ctl, uint32_t* bar, int32_t st) {
+    raise_status(ctl, st);
+    atomicOr(bar, kAbortBit);
+}
+
 // Grid-wide barrier for a cooperative launch; called by every thread of every CTA.  The arrival
 // counter only grows: the barrier with index gen (1, 2, ...) is passed once it reaches
 // nblocks * gen, so no CTA has to reset it and the last arrival needs no extra release step.
-// Returns false in all threads of a CTA whose wait ran out (the caller then leaves the loop).
-__device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint32_t& gen, int* s_ok) {
+// Returns false in all threads of a CTA whose wait ran out (RBD_ETIMEOUT) or that saw the abort
+// bit (the caller then leaves the loop).
+__device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint32_t& gen, int* s_ok, Ctl* ctl) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         const uint32_t target = nblocks * (++gen);
-        uint32_t seen;
-        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(seen) : "l"(bar) : "memory");
-        if (seen + 1 < target) {
+        uint32_t v;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(bar) : "memory");
+        v += 1;
+        if (!(v & kAbortBit) && v < target) {
             const uint64_t t0 = globaltimer_ns();
-            while (ld_acquire_u32(bar) < target) {
+            while (true) {
+                v = ld_acquire_u32(bar);
+                if ((v & kAbortBit) || v >= target) break;
                 if (globaltimer_ns() - t0 > kBarrierLimitNs) {
-                    ok = 0;
+                    loop_abort(ctl, bar, ST_ETIMEOUT);
+                    v = kAbortBit;
                     break;
                 }
             }
         }
+        if (v & kAbortBit) ok = 0;
         *s_ok = ok;
     }
     __syncthreads();
@@ -183,6 +200,7 @@ struct YStream {
     int64_t d_max;
     int R, LC;          // R: column stride of the slice (floats)
     uint64_t pol;
+    uint32_t* bar;      // grid-barrier word (abort bit on a timeout)
     uint32_t count;     // chunks streamed so far (all calls): fixes each chunk's buffer and parity
     bool loaded;        // the slice of this step is resident in the ring
     int64_t nloaded;
@@ -238,7 +256,7 @@ __device__ __forceinline__ void ystream(YStream& ys, int64_t k, int np, int tid,
         const int bf = bufof(c);
         const uint32_t par = ((ys.count + (uint32_t)c) / (uint32_t)ys.NB) & 1u;
         if (!reuse && *ys.ok && !mbar_wait(&ys.ybar[bf], par)) {
-            raise_status(ctl, ST_ETIMEOUT);
+            loop_abort(ctl, ys.bar, ST_ETIMEOUT);
             *ys.ok = false;
         }
         const int64_t l0 = c * ys.LC;
@@ -332,6 +350,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     ys.R = RS;
     ys.LC = p.LC;
     ys.pol = l2_policy_evict_normal();
+    ys.bar = p.bar;
     ys.count = 0;
     ys.loaded = false;
     ys.nloaded = 0;
@@ -495,7 +514,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
             for (int64_t i = 0; i < npref; ++i) {
                 if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
-                    raise_status(ctl, ST_ETIMEOUT);
+                    loop_abort(ctl, p.bar, ST_ETIMEOUT);
                     ok = false;
                     npref = i;
                     break;
@@ -567,8 +586,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             if (lane == 0) ctl->fro_last = sqrt(fmax(fs, 0.0));
         }
         if (k > 0) {
-            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;   // barrier 1
-            if (!ok || __ldcg(&ctl->status) != 0) break;
+            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;   // barrier 1
+            if (!ok) break;
             // ---------------- O2: h(l) = sum_b hpart[b](l), k / G coefficients per CTA ----------------
             if (warp < NW) {
                 const int64_t lb0 = (k * b) / G, lb1 = (k * (b + 1)) / G;
@@ -580,8 +599,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                     if (lane == 0) p.h[l] = acc;
                 }
             }
-            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;   // barrier 2
-            if (!ok || __ldcg(&ctl->status) != 0) break;
+            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;   // barrier 2
+            if (!ok) break;
         }
 
         // ---------------- O3: v2 = v1 - Y h, ||v2||^2 partial ----------------
@@ -613,8 +632,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 if (k > 0) block_dots(p.hpart);
             }
         }
-        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 3
-        if (!ok || __ldcg(&ctl->status) != 0) break;
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;  // barrier 3
+        if (!ok) break;
         if constexpr (!WT) {
             // every consumer is past O3, so the ring is free: the first X tiles of the pass (L2
             // hits) load during the stop decision
@@ -626,6 +645,9 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
         // A-norm form: E_cur and the tests of steps 2.2 / 2.4 take ||v2||_A; xi = v2 / nu and the
         // numerical-rank floor stay Euclidean.
         if (warp == 0) {
+            // independent loads first, so that their round trips overlap
+            const double xn2p = (lane == 0) ? __ldg(&p.xn2[piv]) : 0.0;
+            const double frol = (lane == 0 && k > 0 && mode == MODE_FRO_REL) ? __ldcg(&ctl->fro_last) : 0.0;
             double acc = 0.0, acc2 = 0.0;
             #pragma unroll 8
             for (int64_t bb = lane; bb < G; bb += 32) {
@@ -637,11 +659,11 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             if (lane == 0) {
                 const double nuv = sqrt(acc);
                 const double nea = WT ? sqrt(acc2) : nuv;
-                const double xin = sqrt(p.xn2[piv]);
+                const double xin = sqrt(xn2p);
                 int32_t st = STOP_NONE;
                 if (k > 0) {
                     if (mode == MODE_FRO_REL) {
-                        if (__ldcg(&ctl->fro_last) <= fro_tol) st = STOP_TOL;
+                        if (frol <= fro_tol) st = STOP_TOL;
                     } else if (nea <= eps_r) {
                         st = STOP_TOL;
                     }
@@ -682,8 +704,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                         if (lane == 0) p.h[l] = acc;
                     }
                 }
-                if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 3b
-                if (!ok || __ldcg(&ctl->status) != 0) break;
+                if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;  // barrier 3b
+                if (!ok) break;
             }
             // ---------------- O5: z = u - Y g for this block's rows ----------------
             if (warp < NW) {
@@ -693,8 +715,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             ystream_end_step(ys);
             __syncthreads();
             prefetch_x();
-            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 3c
-            if (!ok || __ldcg(&ctl->status) != 0) break;
+            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;  // barrier 3c
+            if (!ok) break;
         }
 
         // ---------------- P: the fused pass of basis k ----------------
@@ -729,7 +751,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 }
                 for (int64_t i = npref; i < nunits; ++i) {
                     if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
-                        raise_status(ctl, ST_ETIMEOUT);
+                        loop_abort(ctl, p.bar, ST_ETIMEOUT);
                         ok = false;
                         break;
                     }
@@ -818,7 +840,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                     }
                 }
                 if (ok && !mbar_wait(&full[s], ph)) {
-                    raise_status(ctl, ST_ETIMEOUT);
+                    loop_abort(ctl, p.bar, ST_ETIMEOUT);
                     ok = false;
                 }
                 const int rows = (int)min((int64_t)MT, p.ldp - t * MT);
@@ -877,8 +899,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 p.pbest_j[b] = bj;
             }
         }
-        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0])) ok = false;  // barrier 4
-        if (!ok || __ldcg(&ctl->status) != 0) break;
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;  // barrier 4
+        if (!ok) break;
 
         // ---------------- A: argmax over CTAs, Frobenius residual ----------------
         if (warp == 0) {
