@@ -163,6 +163,18 @@ __device__ __forceinline__ double warp_sum_double(double v) {
     return v;
 }
 
+// 1 / x for a positive FP64 x by Newton's iteration y <- y + y (1 - x y) from the FP32
+// reciprocal (relative error 2^-23, squared by each step: two steps reach FP64 rounding, within
+// about 1 ulp) -- four FP64 FMAs instead of a division, whose FP64 sequence is long on this part.
+// Outside the FP32 range it divides.
+__device__ __forceinline__ double recip_pos(double x) {
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / x;
+    double y = (double)__frcp_rn((float)x);
+    y = fma(y, fma(-x, y, 1.0), y);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return y;
+}
+
 // (value, index) max with ties to the lowest index; invalid entries carry index INT64_MAX.
 __device__ __forceinline__ bool better(double e1, int64_t j1, double e0, int64_t j0) {
     return (e1 > e0) || (e1 == e0 && j1 < j0);

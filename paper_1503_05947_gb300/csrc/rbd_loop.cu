@@ -671,7 +671,9 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 if (st == STOP_NONE && k >= p.d_max) st = STOP_DMAX;
                 if (st == STOP_NONE && (nea < eps_r22 || nuv <= kRankFloor * xin)) st = STOP_BREAK;
                 bcast[0] = nuv;
-                bcast[3] = (WT && acc > 0.0) ? acc2 / acc : 1.0;  // xi' A xi
+                const double inv = recip_pos(nuv);
+                bcast[1] = inv;                                   // once, for every thread of the pass
+                bcast[3] = (WT && acc > 0.0) ? acc2 * (inv * inv) : 1.0;  // xi' A xi
                 sflags[1] = st;
                 if (b == 0) {
                     if (k > 0) {
@@ -720,7 +722,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
         }
 
         // ---------------- P: the fused pass of basis k ----------------
-        const double inv_nu = 1.0 / nu;
+        const double inv_nu = bcast[1];
         // Y(:, k) = v2 / nu for this block's rows (user Y and the split row-block copy)
         for (int r = tid; r < Rb; r += Cfg::THREADS) {
             const double y = v2own[r] * inv_nu;
@@ -924,17 +926,13 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                     bj = oj;
                 }
             }
-            if (lane == 0) {
-                bcast[2] = sqrt(fmax(be, 0.0));
-                red_j[0] = (bj >= 0 && bj < p.n) ? bj : piv;
-            }
+            if (lane == 0) red_j[0] = (bj >= 0 && bj < p.n) ? bj : piv;
         }
         __syncthreads();
         piv = red_j[0];
         if (b == 0 && tid == 0) {
             ctl->d = k + 1;
             ctl->pivot = piv;
-            ctl->err_downdate = bcast[2];
         }
         __syncthreads();
     }
