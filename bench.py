@@ -298,7 +298,7 @@ def run_gpu(args, world, rank, local):
         # the persistent kernel runs the whole greedy loop: per launch it streams X once per basis
         kern_s = loop_ms / loop_n / 1e3
         bytes_per_launch = bytes_per_pass * loop_passes / loop_n
-        kname = "rbd::loop_kernel<0> (persistent greedy loop: fused passes + orthogonalisation)"
+        kname = "rbd::loop_kernel<0, 0> (persistent greedy loop: fused passes + orthogonalisation)"
     else:
         kern_s = pass_ms / max(pass_n, 1) / 1e3
         bytes_per_launch = bytes_per_pass
