@@ -194,7 +194,7 @@ rbd_status rbd_compress_resume(const void* X, rbd_dtype xt, int64_t m, int64_t n
  * NULL) are HOST pointers.  The call allocates device buffers stream-ordered, copies X to
  * the device, runs the loop, copies the first d columns/rows/entries back and frees the
  * device buffers.  Pinned host buffers make the copies asynchronous DMA transfers; pageable
- * ones work but are staged by the driver.  Returns after the results are in host memory.
+ * ones work but are staged by the CUDA driver.  Returns after the results are in host memory.
  */
 rbd_status rbd_compress_host(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
                              double tol, rbd_tol_mode mode, int64_t d_max, int64_t start,
