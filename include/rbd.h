@@ -165,6 +165,26 @@ rbd_status rbd_compress_weighted(const void* X, rbd_dtype xt, int64_t m, int64_t
                                  void* stream, rbd_result* result);
 
 /*
+ * rbd_compress_rows -- the row-space form (Section 3.1: each column of the data matrix is an
+ * entry, "or row if we are compressing the row space"): Algorithm 1 on the ROWS of X, i.e.
+ * rbd_compress applied to X' (n x m).
+ *
+ *  X       [in]  device, m x n column-major, ldx >= m, storage type xt (read only).  The call
+ *                transposes it once into a stream-ordered scratch copy of m * n elements.
+ *  start   [in]  0 <= start < m: the row of step 1.
+ *  Y       [out] device, n x d_max, column-major, ldy >= n: the bases of the row space.
+ *  T       [out] device, d_max x m, column-major, ldt >= d_max: T(k, i) = xi_k' X(i, :)'.
+ *  pivots  [out] row indices of X; err, nu, result as rbd_compress (over rows).
+ *  Requires 1 <= d_max <= min(m, n).  Errors as rbd_compress; RBD_ENOMEM if the scratch copy
+ *  cannot be allocated.  The workspace is always library-allocated.
+ */
+rbd_status rbd_compress_rows(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
+                             double tol, rbd_tol_mode mode, int64_t d_max, int64_t start,
+                             double* Y, int64_t ldy, double* T, int64_t ldt,
+                             int64_t* pivots, double* err, double* nu,
+                             void* stream, rbd_result* result);
+
+/*
  * rbd_compress_resume -- continue a compression to a larger d_max: Algorithm 1's loop picks up
  * after d0 bases from its outputs (a checkpoint of the greedy state).
  *

@@ -13,6 +13,7 @@ from .rbd import (  # noqa: F401
     compress_host,
     compress_noalloc,
     compress_resume,
+    compress_rows,
     grad,
     get_profile,
     load,

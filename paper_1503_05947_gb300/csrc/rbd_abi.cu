@@ -568,6 +568,40 @@ rbd_status rbd_compress_resume(const void* X, rbd_dtype xt, int64_t m, int64_t n
                            workspace, workspace_bytes, (cudaStream_t)stream, result, d0, next_pivot);
 }
 
+rbd_status rbd_compress_rows(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol,
+                             rbd_tol_mode mode, int64_t d_max, int64_t start, double* Y, int64_t ldy, double* T,
+                             int64_t ldt, int64_t* pivots, double* err, double* nu, void* stream,
+                             rbd_result* result) {
+    // the problem on X' (n x m): its columns are the rows of X
+    if (!X || m < 1 || n < 1 || ldx < m) return RBD_EINVAL;
+    rbd_status v = validate(X, xt, n, m, n, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err);
+    if (v != RBD_OK) return v;
+    DeviceState ds;
+    cudaError_t ce = device_state(ds);
+    if (ce != cudaSuccess) return map_cuda(ce);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int es = (xt == RBD_F64) ? 8 : (xt == RBD_F32 ? 4 : 2);
+    void* Xt = nullptr;
+    ce = cudaMallocAsync(&Xt, (size_t)m * (size_t)n * es, st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return RBD_ENOMEM;
+    }
+    rbd_status rs = RBD_OK;
+    ce = launch_transpose(X, es, m, n, ldx, Xt, ds.num_sms, st);
+    if (ce == cudaSuccess)
+        rs = compress_device(Xt, xt, n, m, n, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err, nu, nullptr, 0,
+                             st, result);
+    cudaError_t fe = cudaFreeAsync(Xt, st);
+    if (ce == cudaSuccess) ce = fe;
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return map_cuda(ce);
+    }
+    if (result && rs == RBD_OK) result->launches += 1;
+    return rs;
+}
+
 rbd_status rbd_compress_host(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol,
                              rbd_tol_mode mode, int64_t d_max, int64_t start, double* Y, int64_t ldy,
                              double* T, int64_t ldt, int64_t* pivots, double* err, double* nu, void* stream,

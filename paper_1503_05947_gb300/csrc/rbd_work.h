@@ -198,6 +198,10 @@ cudaError_t launch_project(const double* Y, int64_t m, int64_t d, int64_t ldy, c
 // copy of Y for the path in use, and fro_last / pivot / d in the control block.
 cudaError_t launch_resume(const Work& w, const double* Y, int64_t ldy, const double* T, int64_t ldt,
                           const int64_t* pivots, int64_t k0, int64_t next_pivot, cudaStream_t st);
+// Xt(j, i) = X(i, j) for an m x n column-major X (ldx) and the n x m column-major Xt (ld = n); esize
+// is the element size in bytes (8, 4 or 2).
+cudaError_t launch_transpose(const void* X, int esize, int64_t m, int64_t n, int64_t ldx, void* Xt, int num_sms,
+                             cudaStream_t st);
 cudaError_t launch_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy, const double* T, int64_t n,
                                int64_t ldt, double* Xr, int64_t ldxr, cudaStream_t st);
 // Dynamic shared-memory opt-in for the pass kernels and their resident CTAs per SM, indexed by

@@ -83,6 +83,9 @@ def load():
     lib.rbd_compress_weighted.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _PTR, _DBL, ctypes.c_int, _I64, _I64,
                                           _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.c_size_t, _PTR,
                                           ctypes.POINTER(_Result)]
+    lib.rbd_compress_rows.restype = ctypes.c_int
+    lib.rbd_compress_rows.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
+                                      _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.POINTER(_Result)]
     lib.rbd_compress_host.restype = ctypes.c_int
     lib.rbd_compress_host.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _DBL, ctypes.c_int, _I64, _I64,
                                       _PTR, _I64, _PTR, _I64, _PTR, _PTR, _PTR, _PTR, ctypes.POINTER(_Result)]
@@ -220,6 +223,32 @@ def compress(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: 
                                            T.data_ptr(), d_max, piv.data_ptr(), err.data_ptr(), nu.data_ptr(),
                                            ws_ptr, ws_bytes, _stream_ptr(dev), ctypes.byref(res))
     _check(st, "rbd_compress" if weights is None else "rbd_compress_weighted")
+    d = int(res.d)
+    return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
+                      STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),
+                      float(res.x_fro), float(res.x_maxcol), int(res.launches))
+
+
+def compress_rows(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: str = "maxcol_abs") -> Compressed:
+    """rbd_compress_rows: Algorithm 1 on the ROWS of the column-major CUDA tensor X (m x n), i.e.
+    the compression of X' (the row space of Section 3.1).  Y is n x d, T is d x m, pivots are rows."""
+    lib = load()
+    if not X.is_cuda or X.dtype not in DTYPES:
+        raise ValueError("X must be a CUDA tensor of a supported dtype")
+    m, n = X.shape
+    ldx = _colmajor(X, "X")
+    dev = X.device
+    Y = colmajor_empty(n, d_max, torch.float64, dev)
+    T = colmajor_empty(d_max, m, torch.float64, dev)
+    piv = torch.empty(d_max, dtype=torch.int64, device=dev)
+    err = torch.empty(d_max, dtype=torch.float64, device=dev)
+    nu = torch.empty(d_max, dtype=torch.float64, device=dev)
+    res = _Result()
+    with torch.cuda.device(dev):
+        st = lib.rbd_compress_rows(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, float(tol), TOL_MODES[tol_mode],
+                                   int(d_max), int(start), Y.data_ptr(), n, T.data_ptr(), d_max, piv.data_ptr(),
+                                   err.data_ptr(), nu.data_ptr(), _stream_ptr(dev), ctypes.byref(res))
+    _check(st, "rbd_compress_rows")
     d = int(res.d)
     return Compressed(Y[:, :d], T[:d, :], piv[:d], err[:d], nu[:d], d, int(res.next_pivot),
                       STOP_REASONS.get(int(res.stop_reason), "?"), float(res.err_last), float(res.fro_last),

@@ -95,6 +95,18 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     assert wcall(ctypes.c_void_p(20)) == 1   # not 8-byte aligned
     assert wcall(P, X=None) == 1
     assert wcall(P, d_max=9) == 1
+    # the row-space form: start indexes rows, Y is n x d (ldy >= n), T is d x m
+    def rcall(**kw):
+        a = dict(X=P, m=8, n=6, ldx=8, d_max=4, start=0, ldy=6, ldt=4)
+        a.update(kw)
+        return lib.rbd_compress_rows(a["X"], 0, a["m"], a["n"], a["ldx"], 0.0, 0, a["d_max"], a["start"], P, a["ldy"],
+                                     P, a["ldt"], P, P, None, None, ctypes.byref(res))
+
+    assert rcall(X=None) == 1
+    assert rcall(ldx=7) == 1
+    assert rcall(start=8) == 1       # start < m (a row)
+    assert rcall(ldy=5) == 1         # ldy >= n
+    assert rcall(d_max=7) == 1       # d_max <= min(m, n)
     assert lib.rbd_project(P, 0, 2, 1, P, 0, 1, 1, P, 2, None) == 1
     assert lib.rbd_project(P, 4, 2, 3, P, 0, 1, 4, P, 2, None) == 1   # ldy < m
     assert lib.rbd_project(P, 4, 0, 4, P, 0, 1, 4, P, 1, None) == 0   # d = 0: no-op
