@@ -49,6 +49,7 @@ constexpr int kBMaxD = 512;
 constexpr int kBQR = kBMaxRows / kBNCONS;    // rows per consumer thread
 constexpr int kBRingBytes = 128 * 1024;
 constexpr int kBMaxLC = 64;                  // Y columns per Gram-Schmidt chunk
+constexpr int kBNB = 2;                      // Y chunk buffers (the ring in halves)
 
 template <int P>
 struct BCfg {
@@ -178,12 +179,13 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
     float* ring = reinterpret_cast<float*>(bsm);                               // kBRingBytes
     uint64_t* full = reinterpret_cast<uint64_t*>(bsm + kBRingBytes);           // SMAX
     uint64_t* empty = full + SMAX;                                             // SMAX
-    uint64_t* ybar = empty + SMAX;                                             // 2
-    float* vh = reinterpret_cast<float*>(ybar + 2);                            // kBMaxRows
+    uint64_t* ybar = empty + SMAX;                                             // kBNB
+    float* vh = reinterpret_cast<float*>(ybar + kBNB);                         // kBMaxRows
     float* vl = vh + kBMaxRows;                                                // kBMaxRows
     double* hacc = reinterpret_cast<double*>(vl + kBMaxRows);                  // kBMaxD
-    float* coef = reinterpret_cast<float*>(hacc + kBMaxD);                     // 2 x 2 x kBMaxLC
-    float* wps = coef + 4 * kBMaxLC;                                           // kBNW x kBMaxLC (ff hi)
+    float* cst_h = reinterpret_cast<float*>(hacc + kBMaxD);                    // kBMaxD: coefficients (hi)
+    float* cst_l = cst_h + kBMaxD;                                             // kBMaxD: (lo)
+    float* wps = cst_l + kBMaxD;                                               // kBNW x kBMaxLC (ff hi)
     float* wpc = wps + kBNW * kBMaxLC;                                         // (ff lo)
     double* red = reinterpret_cast<double*>(wpc + kBNW * kBMaxLC);             // 4 kBNW + 16
     int64_t* redj = reinterpret_cast<int64_t*>(red + 2 * kBNW);
@@ -198,8 +200,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kBNW);
         }
-        mbar_init(&ybar[0], 1);
-        mbar_init(&ybar[1], 1);
+        for (int bq = 0; bq < kBNB; ++bq) mbar_init(&ybar[bq], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -284,19 +285,20 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
         double fro_prev = x_fro, err_last = 0.0;
         int32_t stop = (st0 != ST_OK) ? STOP_BREAK : STOP_NONE;
         int64_t k = 0;
-        // Y chunk geometry: the ring as two buffers of half its size, both planes per chunk
-        const int LC = (int)min((int64_t)kBMaxLC, (int64_t)(kBRingBytes / 8) / (2 * rb));
-        const int64_t buf_f = kBRingBytes / 8;  // floats per buffer
+        // Y chunk geometry: the ring as kBNB buffers, both planes per chunk (few large chunks: each
+        // chunk costs two barriers, more than its copy latency)
+        const int64_t buf_f = kBRingBytes / 4 / kBNB;  // floats per buffer
+        const int LC = (int)max((int64_t)1, min((int64_t)kBMaxLC, buf_f / (2 * rb)));
 
-        // streams columns [0, k) of this member's Y block in chunks through the two ring buffers
-        // (consumer threads); stage(l, hi, lo) gives the coefficient of column l,
-        // body(yh, yl, ch, cl, l0, lc) runs on the chunk, post(l0, lc) after the barrier that
-        // closes it.  Every barrier is reached by all consumer threads whatever their waits
-        // returned.
+        // streams columns [0, k) of this member's Y block in chunks through the ring buffers, up
+        // to kBNB in flight (consumer threads); stage(l, hi, lo) gives the coefficient of column l
+        // (all k staged once, before the first chunk), body(yh, yl, ch, cl, l0, lc) runs on the
+        // chunk, post(l0, lc) after the barrier that closes it.  Every barrier is reached by all
+        // consumer threads whatever their waits returned.
         auto ystream = [&](auto&& stage, auto&& body, auto&& post) {
             const int64_t nch = ceil_div(k, (int64_t)LC);
             auto issue = [&](int64_t c) {
-                const int bf = (int)((ycount + (uint32_t)c) & 1u);
+                const int bf = (int)((ycount + (uint32_t)c) % (uint32_t)kBNB);
                 const int64_t l0 = c * LC;
                 const int lc = (int)min((int64_t)LC, k - l0);
                 const uint32_t bytes = (uint32_t)(lc * rb * 4);
@@ -304,22 +306,21 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 bulk_g2s(ring + bf * buf_f, ysb + l0 * rb, bytes, &ybar[bf], pol_y);
                 bulk_g2s(ring + bf * buf_f + (int64_t)LC * rb, ysb + (dmax + l0) * rb, bytes, &ybar[bf], pol_y);
             };
-            if (tid == 0 && nch > 0) issue(0);
+            if (tid == 0)
+                for (int64_t c = 0; c < min(nch, (int64_t)kBNB); ++c) issue(c);
+            for (int64_t l = tid; l < k; l += kBNCONS) stage(l, cst_h[l], cst_l[l]);
             for (int64_t c = 0; c < nch; ++c) {
-                // buffer (c + 1) & 1 was read by chunk c - 1, finished at the barrier below
-                if (tid == 0 && c + 1 < nch) issue(c + 1);
-                const int bf = (int)((ycount + (uint32_t)c) & 1u);
+                // coefficients visible (first chunk); post of chunk c - 1 done before body reuses its scratch
+                named_bar(1, kBNCONS);
+                const int bf = (int)((ycount + (uint32_t)c) % (uint32_t)kBNB);
                 const int64_t l0 = c * LC;
                 const int lc = (int)min((int64_t)LC, k - l0);
-                float* ch = coef + bf * 2 * kBMaxLC;
-                float* cl = ch + kBMaxLC;
-                for (int l = tid; l < lc; l += kBNCONS) stage(l0 + l, ch[l], cl[l]);
-                named_bar(1, kBNCONS);
-                const uint32_t par = ((ycount + (uint32_t)c) >> 1) & 1u;
+                const uint32_t par = ((ycount + (uint32_t)c) / (uint32_t)kBNB) & 1u;
                 if (ok && !mbar_wait(&ybar[bf], par)) ok = false;
-                if (ok) body(ring + bf * buf_f, ring + bf * buf_f + (int64_t)LC * rb, ch, cl, l0, lc);
-                named_bar(1, kBNCONS);
+                if (ok) body(ring + bf * buf_f, ring + bf * buf_f + (int64_t)LC * rb, cst_h + l0, cst_l + l0, l0, lc);
+                named_bar(1, kBNCONS);  // chunk c consumed: its buffer may be refilled
                 post(l0, lc);
+                if (tid == 0 && c + kBNB < nch) issue(c + kBNB);
             }
             ycount += (uint32_t)nch;
         };
@@ -480,6 +481,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     }
                 }
                 bc[3] = nuv;
+                bc[7] = recip_pos(nuv);  // once, for every thread
                 flag[1] = st;
             }
             __syncthreads();
@@ -489,7 +491,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
             if (stop != STOP_NONE) break;
 
             // ---- xi = v2 / nu: the whole vector for the pass; this member's rows of Y(:, k)
-            const double inv_nu = 1.0 / nuv;
+            const double inv_nu = bc[7];
             if (warp < kBNW) {
                 for (int64_t r = tid; r < ldp; r += kBNCONS) {
                     const double y = ((double)vh[r] + (double)vl[r]) * inv_nu;
@@ -535,9 +537,11 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 for (int qq = 0; qq < kBCPW; ++qq)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
+                // lanes 0 and 1 finalise one column each (their FP64 work runs side by side)
+                static_assert(kBCPW == 2, "two columns per consumer warp");
                 double best_e = -1.0, esum = 0.0;
                 int64_t best_j = INT64_MAX;
-                double e_old[kBCPW] = {0.0, 0.0};
+                double e_old = 0.0;
                 int64_t g = g_lo, t = 0;
                 for (int64_t u = 0; u < W; ++u) {
                     const int s = cs;
@@ -548,12 +552,9 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     }
                     const int64_t c0 = g * kBC;
                     const int ncols = (int)min((int64_t)kBC, n - c0);
-                    if (t == 0 && lane == 0) {
-#pragma unroll
-                        for (int qq = 0; qq < kBCPW; ++qq) {
-                            const int cw = warp * kBCPW + qq;
-                            e_old[qq] = (cw < ncols) ? __ldcg(&I.e[c0 + cw]) : 0.0;
-                        }
+                    if (t == 0 && lane < kBCPW) {
+                        const int cw = warp * kBCPW + lane;
+                        e_old = (cw < ncols) ? __ldcg(&I.e[c0 + cw]) : 0.0;
                     }
                     if (ok && !mbar_wait(&full[s], ph)) ok = false;
                     const int rows = (int)min((int64_t)kBMT, ldp - t * kBMT);
@@ -571,6 +572,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     if (++t < NT) continue;
                     t = 0;
                     // end of column group g: T(k, j), e_j, the running argmax
+                    float fsq[kBCPW], fcq[kBCPW];
 #pragma unroll
                     for (int qq = 0; qq < kBCPW; ++qq) {
                         float sq = acc_s[qq][0], cq = acc_c[qq][0];
@@ -579,12 +581,17 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                         warp_sum_ff(sq, cq);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
-                        const int cw = warp * kBCPW + qq;
-                        if (lane == 0 && cw < ncols) {
+                        fsq[qq] = sq;
+                        fcq[qq] = cq;
+                    }
+                    const float s1 = __shfl_sync(0xffffffffu, fsq[1], 0), c1 = __shfl_sync(0xffffffffu, fcq[1], 0);
+                    if (lane < kBCPW) {
+                        const int cw = warp * kBCPW + lane;
+                        if (cw < ncols) {
                             const int64_t j = c0 + cw;
-                            const double cj = ff_to_double(sq, cq);
+                            const double cj = (lane == 0) ? ff_to_double(fsq[0], fcq[0]) : ff_to_double(s1, c1);
                             I.T[j * I.ldt + k] = cj;
-                            const double en = (j == piv) ? 0.0 : fmax(e_old[qq] - cj * cj, 0.0);
+                            const double en = (j == piv) ? 0.0 : fmax(e_old - cj * cj, 0.0);
                             I.e[j] = en;
                             esum += en;
                             if (better(en, j, best_e, best_j)) {
@@ -595,10 +602,19 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     }
                     ++g;
                 }
-                if (lane == 0) {
-                    red[warp] = best_e;
-                    redj[warp] = best_j;
-                    red[kBNW + warp] = esum;
+                {
+                    const double be1 = __shfl_sync(0xffffffffu, best_e, 1);
+                    const int64_t bj1 = __shfl_sync(0xffffffffu, best_j, 1);
+                    const double es1 = __shfl_sync(0xffffffffu, esum, 1);
+                    if (lane == 0) {
+                        if (better(be1, bj1, best_e, best_j)) {
+                            best_e = be1;
+                            best_j = bj1;
+                        }
+                        red[warp] = best_e;
+                        redj[warp] = best_j;
+                        red[kBNW + warp] = esum + es1;
+                    }
                 }
             }
             ok = __syncthreads_and(ok) != 0;
@@ -672,8 +688,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
 
 template <int P>
 size_t batch_smem() {
-    return (size_t)kBRingBytes + (size_t)(2 * BCfg<P>::SMAX + 2) * 8 + (size_t)2 * kBMaxRows * 4 + (size_t)kBMaxD * 8 +
-           (size_t)4 * kBMaxLC * 4 + (size_t)2 * kBNW * kBMaxLC * 4 + (size_t)(4 * kBNW + 16) * 8;
+    return (size_t)kBRingBytes + (size_t)(2 * BCfg<P>::SMAX + kBNB) * 8 + (size_t)2 * kBMaxRows * 4 + (size_t)kBMaxD * 8 +
+           (size_t)2 * kBMaxD * 4 + (size_t)2 * kBNW * kBMaxLC * 4 + (size_t)(4 * kBNW + 16) * 8;
 }
 
 }  // namespace
