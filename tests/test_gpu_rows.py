@@ -43,6 +43,22 @@ def test_rows_equal_compress_of_transpose(rbd, m, n, dtype):
     assert int(a.pivots.max()) < m
 
 
+@pytest.mark.parametrize("m,n", [(1, 9), (9, 1), (2, 3), (129, 130)])
+def test_rows_degenerate_shapes(rbd, oracle_mod, m, n):
+    """One row, one column, tiny and just-past-a-tile shapes: the transpose's ragged tiles."""
+    rng = np.random.default_rng(m * 31 + n)
+    Xn = np.asfortranarray(rng.standard_normal((m, n)))
+    d = min(m, n)
+    r = rbd.compress_rows(to_device(Xn), 0.0, d)
+    ref = oracle_mod.compress(np.asfortranarray(Xn.T), 0.0, d, 0)
+    assert r.d == ref["d"]
+    assert np.array_equal(r.pivots.cpu().numpy(), ref["pivots"])
+    if r.d:
+        assert np.linalg.norm(to_numpy(r.Y) - ref["Y"], axis=0).max() <= TOL
+        scale = np.linalg.norm(Xn, axis=1)
+        assert (np.abs(to_numpy(r.T) - ref["T"]) / scale[None, :]).max() <= TOL
+
+
 def test_rows_match_oracle(rbd, oracle_mod):
     Xn = gen.decay_matrix_c1(seed=3, noise_sigma=1e-5, m=300, n=1100)
     X = to_device(Xn)
