@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
                     else if (XT == 1) x[q] = (double)((const float*)p.X)[j * p.ldx + r];
                     else x[q] = (double)__bfloat162float(((const __nv_bfloat16*)p.X)[j * p.ldx + r]);
                 }
-                if (!isfinite(x[q])) {
+                // exponent field all ones: Inf or NaN (an integer test: FP64 comparisons are slow here)
+                if ((((unsigned long long)__double_as_longlong(x[q]) >> 52) & 0x7ffu) == 0x7ffu) {
                     bad = ST_ENONFINITE;
                     x[q] = 0.0;
                 }
@@ -100,7 +101,9 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
                 float hi[4], lo[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    if (fabs(x[q]) >= 0x1p127) bad = (bad == ST_OK) ? ST_EUNSUPPORTED : bad;
+                    // |x| >= 2^127 (biased exponent >= 1023 + 127): outside the split's FP32 range
+                    if ((((unsigned long long)__double_as_longlong(x[q]) >> 52) & 0x7ffu) >= 1150u)
+                        bad = (bad == ST_OK) ? ST_EUNSUPPORTED : bad;
                     split_f64_fast(x[q], hi[q], lo[q]);
                     ff_mac2(s, cc, hi[q], lo[q], hi[q], lo[q]);
                 }
