@@ -122,38 +122,51 @@ __global__ void __launch_bounds__(256) batch_init_kernel(BatchParams bp) {
             if (bp.colstart[mid] <= q) lo = mid;
             else hi = mid - 1;
         }
-        const BInst& I = bp.inst[lo];
+        // the fields this loop needs, in registers (the plane stores could alias the table)
+        const BInst& Ig = bp.inst[lo];
+        const void* IX = Ig.X;
+        const int64_t Im = Ig.m, In = Ig.n, Ildx = Ig.ldx, Ildp = Ig.ldp;
+        float* Iplanes = Ig.planes;
+        double* Ie = Ig.e;
+        double* Ixn2 = Ig.xn2;
         const int64_t j = q - bp.colstart[lo];
         const int64_t g = j / kBC;
         const int c = (int)(j % kBC);
-        const bool live = j < I.n;
+        const bool live = j < In;
         float s = 0.f, cc = 0.f;
         int bad = ST_OK;
-        for (int64_t r0 = 4 * lane; r0 < I.ldp; r0 += 128) {
+        for (int64_t r0 = 4 * lane; r0 < Ildp; r0 += 128) {
             const int64_t t = r0 / kBMT;
-            const int64_t rt = min((int64_t)kBMT, I.ldp - t * kBMT);
-            const int64_t base = g * kBC * P * I.ldp + t * kBC * P * kBMT + (int64_t)c * P * rt + (r0 - t * kBMT);
+            const int64_t rt = min((int64_t)kBMT, Ildp - t * kBMT);
+            const int64_t base = g * kBC * P * Ildp + t * kBC * P * kBMT + (int64_t)c * P * rt + (r0 - t * kBMT);
             float hv[4], lv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t r = r0 + u;
-                double x = 0.0;
-                if (live && r < I.m) x = (P == 2) ? ((const double*)I.X)[j * I.ldx + r] : (double)((const float*)I.X)[j * I.ldx + r];
-                if (!isfinite(x)) {
-                    bad = ST_ENONFINITE;
-                    x = 0.0;
-                }
-                if (P == 2 && fabs(x) >= 0x1p127 && bad == ST_OK) bad = ST_EUNSUPPORTED;
-                if (P == 2) {
-                    split_double(x, hv[u], lv[u]);
+                // finiteness and range on the exponent bits (integer tests; the FP64 pipe is slow)
+                if constexpr (P == 2) {
+                    double x = (live && r < Im) ? ((const double*)IX)[j * Ildx + r] : 0.0;
+                    const uint32_t ex = (uint32_t)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffu);
+                    if (ex == 0x7ffu) {
+                        bad = ST_ENONFINITE;
+                        x = 0.0;
+                    } else if (ex >= 1150u && bad == ST_OK) {
+                        bad = ST_EUNSUPPORTED;  // |x| >= 2^127
+                    }
+                    split_f64_fast(x, hv[u], lv[u]);
                     ff_mac2(s, cc, hv[u], lv[u], hv[u], lv[u]);
                 } else {
-                    hv[u] = (float)x;
+                    float x = (live && r < Im) ? ((const float*)IX)[j * Ildx + r] : 0.f;
+                    if ((__float_as_uint(x) & 0x7f800000u) == 0x7f800000u) {
+                        bad = ST_ENONFINITE;
+                        x = 0.f;
+                    }
+                    hv[u] = x;
                     lv[u] = 0.f;
-                    ff_mac1(s, cc, hv[u], hv[u], 0.f);
+                    ff_mac1(s, cc, x, x, 0.f);
                 }
             }
-            float* ph = I.planes + base;
+            float* ph = Iplanes + base;
             *reinterpret_cast<float4*>(ph) = make_float4(hv[0], hv[1], hv[2], hv[3]);
             if (P == 2) *reinterpret_cast<float4*>(ph + rt) = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
@@ -161,8 +174,8 @@ __global__ void __launch_bounds__(256) batch_init_kernel(BatchParams bp) {
         const int anybad = __reduce_max_sync(0xffffffffu, bad);
         if (lane == 0) {
             if (live) {
-                I.e[j] = tsum;
-                I.xn2[j] = tsum;
+                Ie[j] = tsum;
+                Ixn2[j] = tsum;
             }
             if (anybad != ST_OK) atomicCAS(&bp.status[lo], 0, anybad);
         }

@@ -25,26 +25,6 @@ struct InitParams {
     int64_t d_max;
 };
 
-// Split an FP64 value into FP32 hi + lo with integer operations only (no FP64 pipe):
-// hi keeps the sign, exponent and leading 24 significant bits (truncated); lo is the exact
-// remainder r * 2^(E-1075) (r < 2^29) rounded to 24 bits.  |x - hi - lo| <= 2^-48 |x|.
-// Values outside 2^-74 <= |x| < 2^127 take the FP64 conversion path.
-__device__ __forceinline__ void split_f64_fast(double x, float& hi, float& lo) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
-    const int E = (int)((bh >> 20) & 0x7ffu);
-    if (E >= 949 && E <= 1149) {
-        const uint32_t sign = bh & 0x80000000u;
-        const uint32_t mant23 = ((bh & 0xfffffu) << 3) | (bl >> 29);
-        hi = __uint_as_float(sign | ((uint32_t)(E - 896) << 23) | mant23);
-        const uint32_t r = bl & 0x1fffffffu;
-        const float scale = __uint_as_float((uint32_t)(E - 948) << 23);  // 2^(E-1075)
-        lo = __uint_as_float(__float_as_uint(__fmul_rn(__uint2float_rn(r), scale)) | sign);
-    } else {
-        split_double(x, hi, lo);
-    }
-}
-
 // One warp per column of the plane layout; lane l handles rows 4l..4l+3 of every 128-row chunk.
 template <int XT>
 __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
