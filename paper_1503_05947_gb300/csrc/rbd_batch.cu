@@ -607,7 +607,10 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                             const double en = (j == piv) ? 0.0 : fmax(e_old - cj * cj, 0.0);
                             I.e[j] = en;
                             esum += en;
-                            if (better(en, j, best_e, best_j)) {
+                            // en >= 0 and best_e >= 0 or -1: the order of the values is that of their
+                            // bit patterns as signed integers (integer compares: the FP64 pipe is slow)
+                            const long long eb = __double_as_longlong(en), bb = __double_as_longlong(best_e);
+                            if (eb > bb || (eb == bb && j < best_j)) {
                                 best_e = en;
                                 best_j = j;
                             }
