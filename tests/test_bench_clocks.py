@@ -58,3 +58,23 @@ def test_sampler_reads_a_running_nvidia_smi(tmp_path, monkeypatch):
     assert out["samples"] >= 1 and out["sm_mhz"] == 2070.0 and out["reasons"] == []
     args = (tmp_path / "args.txt").read_text()
     assert "-i 3" in args and "--query-gpu=" in args and "-lms 100" in args
+
+
+def test_traffic_is_reported_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):
+    """`roofline.traffic` comes from the committed ncu summary only while the hash of the kernel
+    sources it records matches the current sources."""
+    import json
+    import shutil
+
+    for rel in bench.PASS_SOURCES:
+        dst = tmp_path / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(ROOT, rel), dst)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    path = tmp_path / "profiles" / "loop_kernel_image8192_f64_traffic.json"
+    path.write_text(json.dumps({"source_hash": bench.pass_kernel_hash(), "dram_bytes_per_launch": 1.0}))
+    assert bench.ncu_traffic()["dram_bytes_per_launch"] == 1.0
+    with open(tmp_path / bench.PASS_SOURCES[0], "a") as f:
+        f.write("\n// changed\n")
+    assert bench.ncu_traffic() is None
