@@ -70,6 +70,9 @@ CASES = [
      "maxcol_abs", 76),
     ("tall 20000x300", lambda: gen.lowrank_haar(20000, 300, 2.0 ** (-np.arange(300) / 8), seed=8, noise_sigma=1e-9),
      1e-6, 80, "maxcol_rel", 0),
+    # more than 256 rows per CTA (two rows per consumer thread in the Gram-Schmidt phases)
+    ("tall 50000x120", lambda: gen.lowrank_haar(50000, 120, 2.0 ** (-np.arange(120) / 6), seed=9, noise_sigma=1e-9),
+     1e-6, 40, "fro_rel", 5),
 ]
 
 
