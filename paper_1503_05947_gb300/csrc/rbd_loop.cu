@@ -3,7 +3,8 @@
 // One CTA per SM (8 consumer warps + 1 producer warp), all co-resident (cooperative launch), so
 // the steps of the loop are separated by grid-wide barriers instead of kernel launches.  Every
 // barrier and every mbarrier wait is bounded in time (kWaitLimitNs); a wait that runs out raises
-// RBD_ETIMEOUT in the control block and all CTAs leave the loop at the next barrier.
+// RBD_ETIMEOUT in the control block and sets the abort bit of the barrier word, and all CTAs leave
+// the loop at their next barrier.
 //
 // Per basis k (k = 0 .. d_max; the last iteration only certifies E_cur and stops):
 //   O1   v1 = x_i - Y t, t = T(0:k, i)            rows of this CTA's block, float-float
@@ -15,11 +16,12 @@
 //   ---- grid barrier 3
 //   D    nu = ||v2|| (every CTA, fixed order); E_cur of basis k-1 = nu (the FP64 residual of the
 //        column that maximised the indicator); stop tests of steps 2.4 and 2.2, identical in
-//        every CTA
+//        every CTA; 1 / nu once for the pass
 //   P    the fused pass (rbd_tile.cuh): T(k, :), e_j, per-CTA argmax; Y(:, k) = v2 / nu for
 //        this CTA's rows
 //   ---- grid barrier 4
-//   A    argmax over the CTAs (every CTA), Frobenius residual (fixed order)
+//   A    argmax over the CTAs (every CTA); the Frobenius residual of the basis (fixed order) is
+//        summed by CTA 0's producer warp during the next O1, off the critical path
 //
 // The A-norm form (Section 3.2, A = diag(w)) keeps this basis and T, and measures the indicator
 // in ||.||_A.  Adding xi_k changes ||r_j||_A^2 by -2 c_j xi_k' A r_j + c_j^2 xi_k' A xi_k, and
@@ -31,9 +33,9 @@
 //   O5   z = u - Y g for this block's rows (nu is applied in the pass);  ---- grid barrier 3c
 //
 // This is classical Gram-Schmidt applied twice (see rbd_orth.cu for why, and for its accuracy);
-// Y is kept as a split FP32 copy stored ROW-BLOCK-MAJOR (block b = this CTA's R rows, all
-// columns contiguous), so each CTA streams only its own slice of Y, with bulk copies, and no
-// other CTA ever reads it.  X never changes: the producer prefetches the first tiles of the next
+// Y is kept as a split FP32 copy stored ROW-BLOCK-MAJOR (block b = this CTA's R rows, columns
+// RS >= R floats apart, all contiguous), so each CTA streams only its own slice of Y, with bulk
+// copies, and no other CTA ever reads it.  X never changes: the producer prefetches the first tiles of the next
 // pass into L2 while the orthogonalisation runs and into shared memory after barrier 3; only the
 // pivot-vector tiles wait for O3.
 #include <algorithm>

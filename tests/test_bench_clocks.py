@@ -62,7 +62,7 @@ def test_sampler_reads_a_running_nvidia_smi(tmp_path, monkeypatch):
 
 def test_traffic_is_reported_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):
     """`roofline.traffic` comes from the committed ncu summary only while the hash of the kernel
-    sources it records matches the current sources."""
+    code it records (comments excluded) matches the current sources."""
     import json
     import shutil
 
@@ -76,5 +76,8 @@ def test_traffic_is_reported_only_for_the_sources_it_was_taken_on(tmp_path, monk
     path.write_text(json.dumps({"source_hash": bench.pass_kernel_hash(), "dram_bytes_per_launch": 1.0}))
     assert bench.ncu_traffic()["dram_bytes_per_launch"] == 1.0
     with open(tmp_path / bench.PASS_SOURCES[0], "a") as f:
-        f.write("\n// changed\n")
+        f.write("\n// a comment changes nothing\n/* nor does\n   this one */\n")
+    assert bench.ncu_traffic()["dram_bytes_per_launch"] == 1.0
+    with open(tmp_path / bench.PASS_SOURCES[0], "a") as f:
+        f.write("\nstatic const int changed_code = 1;\n")
     assert bench.ncu_traffic() is None
