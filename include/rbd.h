@@ -245,9 +245,12 @@ rbd_status rbd_compress_host(const void* X, rbd_dtype xt, int64_t m, int64_t n, 
  *  capture begins.  The call synchronises `stream` at its end, like rbd_compress.
  *  Calls that overlap on one device (several host threads, or several streams) share the one
  *  array and race: the caller must serialise them.
+ *  result->launches counts the kernels this call enqueued: the stepwise path (RBD_STEPWISE=1,
+ *  or a problem the persistent kernel cannot take) enqueues every step up to d_max, and the
+ *  steps after the stop return at entry, so the count can exceed rbd_compress's.
  *  Errors: those of rbd_compress, and RBD_ENOMEM when the workspace these sizes need
  *  (rbd_compress_workspace_bytes) is larger than RBD_NOALLOC_SCRATCH_BYTES -- for an FP64 X
- *  roughly m * n <= 7 million elements.
+ *  roughly m * n <= 7 million elements (less when d_max is a large fraction of m).
  */
 rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
                                 double tol, rbd_tol_mode mode, int64_t d_max, int64_t start,

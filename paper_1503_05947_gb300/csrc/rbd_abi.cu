@@ -27,6 +27,13 @@ static const int kLookahead = 4;
 // ---------------------------------------------------------------------------------------
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// RBD_LOOP_CLASSIC=1 keeps the four-barrier loop kernel for A = I (for comparisons).
+static bool classic_loop_forced() {
+    const char* v = getenv("RBD_LOOP_CLASSIC");
+    return v && v[0] && v[0] != '0';
+}
+
+
 bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms,
                int pass_ctas_per_sm, int loop_max_smem, int wt) {
     w = Work{};
@@ -72,6 +79,16 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
                 w.RS = (int)RS;
                 w.LC = LC;
                 w.loop_smem = smem;
+            }
+            // A = I: the two-barrier kernel, when its shared memory (the T block grows with d_max) fits
+            const int KC = (int)round_up(d_max, 4);
+            const int LCd = defer_chunk_cols(xt, (int)RS);
+            const size_t smd = defer_smem_bytes(xt, (int)R, KC);
+            if (w.use_loop && !wt && !classic_loop_forced() && LCd >= 4 && smd > 0 && smd <= (size_t)loop_max_smem) {
+                w.use_defer = 1;
+                w.KC = KC;
+                w.LC = LCd;
+                w.loop_smem = smd;
             }
         }
     }
@@ -120,7 +137,8 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     size_t o_h = take((size_t)d_max * 8);
     size_t o_nu2 = take((size_t)std::max<int64_t>(w.RB, lp ? 2 * (int64_t)w.G_loop : 0) * 8);
     size_t o_gslot = take((size_t)(lp ? 2 : 1) * (size_t)w.ngroups * (size_t)w.KMAX * (size_t)w.C * 8);
-    size_t o_gsum = take((size_t)w.ngroups * 8);
+    size_t o_gsum = take((size_t)(w.use_defer ? 2 : 1) * (size_t)w.ngroups * 8);
+    size_t o_tf = take(w.use_defer ? (size_t)w.ngroups * (size_t)d_max * (size_t)w.C * 4 : 0);
     size_t o_pbe = take(gp * 8), o_pbj = take(gp * 8);
     w.total_bytes = off;
     // stash offsets in the pointer fields (carve_work rebases them)
@@ -146,6 +164,7 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     w.nu2part = (double*)o_nu2;
     w.gslot = (double*)o_gslot;
     w.gsum = (double*)o_gsum;
+    w.tf = (float*)o_tf;
     w.pbest_e = (double*)o_pbe;
     w.pbest_j = (int64_t*)o_pbj;
     return true;
@@ -177,6 +196,7 @@ void carve_work(Work& w, void* base) {
     RB_REBASE(nu2part);
     RB_REBASE(gslot);
     RB_REBASE(gsum);
+    RB_REBASE(tf);
     RB_REBASE(pbest_e);
     RB_REBASE(pbest_j);
 #undef RB_REBASE
@@ -185,12 +205,6 @@ void carve_work(Work& w, void* base) {
 // ---------------------------------------------------------------------------------------
 // Per-device state: SM count and one-time kernel attribute setup
 // ---------------------------------------------------------------------------------------
-struct DeviceState {
-    int num_sms = 0;
-    int pass_ctas_per_sm[3] = {1, 1, 1};
-    int loop_max_smem = 0;  // 0: the persistent loop kernel is not used on this device
-    bool ready = false;
-};
 static std::mutex g_dev_mu;
 static DeviceState g_dev[64];
 
@@ -201,7 +215,7 @@ static bool stepwise_forced() {
     return v && v[0] && v[0] != '0';
 }
 
-static cudaError_t device_state(DeviceState& out) {
+cudaError_t device_state(DeviceState& out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -217,7 +231,7 @@ static cudaError_t device_state(DeviceState& out) {
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (coop && optin > 0) {
-            if (loop_kernel_setup(optin) == cudaSuccess)
+            if (loop_kernel_setup(optin) == cudaSuccess && defer_kernel_setup(optin) == cudaSuccess)
                 s.loop_max_smem = optin;
             else
                 cudaGetLastError();
@@ -283,7 +297,7 @@ static void progress_release(int slot) {
 static std::atomic<int> g_profiling{0};
 static thread_local rbd_profile t_profile = {};
 
-static rbd_status map_cuda(cudaError_t e) {
+rbd_status map_cuda(cudaError_t e) {
     if (e == cudaSuccess) return RBD_OK;
     if (e == cudaErrorMemoryAllocation) return RBD_ENOMEM;
     return RBD_ECUDA;
@@ -371,7 +385,8 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
             ev_loop1 = new_event();
             cudaEventRecord(ev_loop0, st);
         }
-        ce = launch_loop(w, X, Y, ldy, T, ldt, pivots, err, nu, k0, st);
+        ce = w.use_defer ? launch_defer(w, X, Y, ldy, T, ldt, pivots, err, nu, k0, st)
+                         : launch_loop(w, X, Y, ldy, T, ldt, pivots, err, nu, k0, st);
         ++launches;
         if (prof) cudaEventRecord(ev_loop1, st);
     }
@@ -500,9 +515,9 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
     return rs;
 }
 
-static rbd_status validate(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol,
-                           rbd_tol_mode mode, int64_t d_max, int64_t start, const double* Y, int64_t ldy,
-                           const double* T, int64_t ldt, const int64_t* pivots, const double* err) {
+rbd_status validate(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol, rbd_tol_mode mode,
+                    int64_t d_max, int64_t start, const double* Y, int64_t ldy, const double* T, int64_t ldt,
+                    const int64_t* pivots, const double* err) {
     if (!X || !Y || !T || !pivots || !err) return RBD_EINVAL;
     if (!valid_dtype((int)xt)) return RBD_EINVAL;
     if (m < 1 || n < 1 || ldx < m || ldy < m || d_max < 1 || ldt < d_max) return RBD_EINVAL;

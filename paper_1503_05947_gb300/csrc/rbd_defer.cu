@@ -1,0 +1,1109 @@
+// rbd_defer.cu -- the greedy loop of Algorithm 1 (A = I) in ONE persistent cooperative kernel with
+// two grid barriers per basis.
+//
+// Basis k applies classical Gram-Schmidt twice to the pivot column x_i (Section 3.1, step 2.2, with
+// one re-orthogonalisation):
+//     v1 = x_i - Y t,   t = Y' x_i = T(0:k, i)        (the first sweep's coefficients are in T)
+//     h  = Y' v1,       v2 = v1 - Y h,   nu = ||v2||,   xi_k = v2 / nu.
+// The fused pass (T(k, :) of step 2.2, the indicator of step 2.3) needs c_j = xi_k' x_j for every
+// column.  Because Y' x_j = T(0:k, j) and Y'Y = I,
+//     c_j = (v1' x_j - h' T(0:k, j)) / nu,        nu^2 = ||v1||^2 - ||h||^2,
+// so X can be streamed as soon as v1 is known.  The grid-wide reduction of the second sweep (h, nu
+// and the stop tests of steps 2.2 and 2.4) runs in a service warp while the pass streams X, and a
+// column's dot product v1' x_j is corrected when its column group is finalised.  v2 and xi_k are
+// formed at the start of the next basis, in the same stream over Y as that basis's first sweep.
+//
+// Per basis k, every CTA (one per SM: 8 consumer warps, a producer warp and a service warp):
+//   F    Y_b(:, 0:k-1) (this CTA's rows, split FP32, row-block-major) streamed once for two row
+//        sums: a = Y h_{k-1} gives v2 = v1_{k-1} - a and xi_{k-1} = v2 / nu_{k-1} = Y(:, k-1);
+//        b = Y t gives v1_k = x_i - b - xi_{k-1} T(k-1, i)
+//   O1'  hpart[b] = Y_b(:, 0:k)' v1_k (the new column from shared memory), the partial ||v1_k||^2,
+//        and v1_k split into the pivot-vector tiles of the pass
+//   ---- grid barrier 1
+//   P    the pass with v1_k: the producer's bulk copies into a ring of stages, float-float dot
+//        products in the consumers (rbd_tile.cuh).  Meanwhile the service warp sums k / G
+//        coefficients of h over the CTAs, waits on a counter for the other CTAs' shares (the
+//        consumers keep streaming), and forms nu and the stop decision.  A group's finaliser
+//        subtracts h' T(0:k, j) and divides by nu.  The term is ||h|| / nu relative to the
+//        column's norm (~4e-12 on the image workload): in FP32 from a group-blocked FP32 copy of
+//        T streamed into shared memory while ||h|| / nu <= 2^-29, else in float-float from T
+//        itself (ill-conditioned steps: T(:, i) is the first sweep of later bases, and an error
+//        there returns amplified by ||x_i|| / nu).
+//   ---- grid barrier 2
+//   A    argmax over the CTAs' candidates (every CTA)
+// A basis that step 2.2 or 2.4 rejects is known once the service warp is done; its pass stops at
+// the next finalised group and writes nothing.  Every wait is bounded (kWaitLimitNs,
+// kBarrierLimitNs); a wait that runs out raises RBD_ETIMEOUT and the abort bit of the barrier
+// word, and the CTAs leave at their next grid barrier after their copies in flight have landed.
+#include <algorithm>
+
+#include "rbd_device.cuh"
+#include "rbd_loop.cuh"
+#include "rbd_tile.cuh"
+#include "rbd_work.h"
+
+namespace rbd {
+
+struct DeferParams {
+    int64_t m, n, ldp, ldx, ldt, ldy, d_max;
+    int64_t k0;           // first basis index of this launch (0, or d0 when resuming)
+    int xt;
+    const unsigned char* planes;
+    int64_t group_stride, tile_stride, NT, ngroups, W;
+    int KMAX;
+    int evict_first;
+    const void* X;
+    double* Y;
+    double* T;
+    int64_t* pivots;
+    double* err;
+    double* nu_out;
+    Ctl* ctl;
+    uint32_t* bar;        // grid barrier word (monotonic arrivals, abort bit)
+    uint32_t* hcnt;       // shares of h published (monotonic, G per basis)
+    double* e;
+    const double* xn2;
+    float* ysb;           // [G][2][d_max][RS] split Y, row-block-major
+    float* vs;            // tile-interleaved split v1 (pivot-vector tiles of the pass)
+    float* tf;            // [ngroups][d_max][C] T in FP32, group-blocked (the flush corrections)
+    double* hpart;        // [G][d_max]
+    double* h;            // [d_max]
+    double* nu2part;      // [G]
+    double* pbest_e;      // [G]
+    int64_t* pbest_j;     // [G]
+    uint32_t* gcnt;
+    double* gslot;
+    double* gsum;         // [2][ngroups]: per-group sums of e_j, by parity of the basis
+    int R, RS, LC, KC;
+};
+
+struct DeferSmem {
+    size_t bars, v1s, xis, v1hl, part, coef, tfb, corr, scratch, total;
+};
+
+// Shared-memory layout (host and device agree through this function).  KC = d_max rounded up to 4.
+template <class Cfg>
+__host__ __device__ inline DeferSmem defer_smem_layout(int R, int KC) {
+    constexpr int NCONS = Cfg::NW * 32;
+    DeferSmem s;
+    size_t o = (size_t)Cfg::S * Cfg::STAGE_FLOATS * 4;  // the ring: pass stages / Y chunks
+    s.bars = o;
+    o += (size_t)(3 * Cfg::S + 2) * 8;              // full, empty, ybar; tfull, svc
+    o = (o + 15) & ~size_t(15);
+    s.v1s = o;
+    o += (size_t)R * 8;                            // v1 (FP64), kept into the next basis
+    s.xis = o;
+    o += (size_t)2 * R * 4;                        // xi_{k-1} split: hi, lo
+    s.v1hl = o;
+    o += (size_t)2 * R * 4;                        // v1 split: hi, lo
+    s.part = o;
+    o += (size_t)2 * NCONS * 8;                    // partial sums of the slice GEMVs
+    s.coef = o;
+    o += (size_t)4 * KC * 4;                       // [h hi | h lo | t hi | t lo]
+    s.tfb = o;
+    o += (size_t)KC * Cfg::C * 4;                  // T(0:k, group) in FP32
+    s.corr = o;
+    o += (size_t)Cfg::NW * Cfg::C * 4;             // flush corrections, per warp
+    s.scratch = o;
+    o += (size_t)(2 * Cfg::NW + 2 * Cfg::C + 8) * 8 + 16 * 4;
+    s.total = (o + 127) & ~size_t(127);
+    return s;
+}
+
+// Spin on the h counter until it reaches target (all lanes of the warp read the same word);
+// false if the abort bit appeared or kBarrierLimitNs elapsed.
+__device__ __forceinline__ bool wait_counter(const uint32_t* cnt, const uint32_t* bar, uint32_t target) {
+    if (ld_acquire_u32(cnt) >= target) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (ld_acquire_u32(cnt) >= target) return true;
+        if ((it & 63u) == 63u) {
+            if (*(volatile const uint32_t*)bar & kAbortBit) return false;
+            if (globaltimer_ns() - t0 > kBarrierLimitNs) return false;
+        }
+    }
+}
+
+template <int XT>
+__global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(DeferParams p) {
+    using Cfg = TileCfg<XT>;
+    constexpr int UB = Cfg::PL * Cfg::ESIZE;  // X bytes per element and column of a unit
+    constexpr int NW = Cfg::NW, CPW = Cfg::CPW, C = Cfg::C, MT = Cfg::MT, S = Cfg::S;
+    constexpr int XI = Cfg::XI_FLOATS, STAGE = Cfg::STAGE_FLOATS;
+    constexpr int NCONS = NW * 32;
+    constexpr int MAXRPT = kLoopMaxRows / NCONS;  // rows per consumer thread when R > NCONS
+    constexpr int NLS = NCONS / C;                // row subsets of a flush correction
+    constexpr int PROD = NW, SVC = NW + 1;        // producer and service warps
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int R = p.R, RS = p.RS, LC = p.LC, KC = p.KC;
+    const DeferSmem L = defer_smem_layout<Cfg>(R, KC);
+    float* stages = reinterpret_cast<float*>(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + L.bars);
+    uint64_t* empty = full + S;
+    uint64_t* ybar = empty + S;
+    uint64_t* tfull = ybar + S;
+    uint64_t* svcb = tfull + 1;
+    double* v1s = reinterpret_cast<double*>(smem_raw + L.v1s);
+    float* xih = reinterpret_cast<float*>(smem_raw + L.xis);
+    float* xil = xih + R;
+    float* v1h = reinterpret_cast<float*>(smem_raw + L.v1hl);
+    float* v1l = v1h + R;
+    double* part = reinterpret_cast<double*>(smem_raw + L.part);
+    float* cah = reinterpret_cast<float*>(smem_raw + L.coef);
+    float* cal = cah + KC;
+    float* cbh = cal + KC;
+    float* cbl = cbh + KC;
+    float* tfb = reinterpret_cast<float*>(smem_raw + L.tfb);
+    float* corr = reinterpret_cast<float*>(smem_raw + L.corr);
+    double* red_e = reinterpret_cast<double*>(smem_raw + L.scratch);  // NW
+    int64_t* red_j = reinterpret_cast<int64_t*>(red_e + NW);          // NW
+    double* grp_e = reinterpret_cast<double*>(red_j + NW);           // 2 C
+    double* bcast = grp_e + 2 * C;                                   // 8: nu, 1/nu, ||h||^2
+    int* sfl = reinterpret_cast<int*>(bcast + 8);
+    // sfl: [0] grid-barrier result  [1] stop decision (service warp)  [2] last-arriver flag of a
+    //      flush  [3] units the producer issued in a cut pass  [4] basis tag of [3]  [5] the
+    //      decision as the consumers read it (one reader, then a barrier: a uniform value)
+    //      [6] float-float flush corrections this basis (service warp)
+    volatile int* vfl = sfl;
+
+    Ctl* ctl = p.ctl;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t G = gridDim.x, b = blockIdx.x;
+    const int64_t r0 = b * (int64_t)R;
+    const int Rb = (int)max((int64_t)0, min((int64_t)R, p.ldp - r0));  // rows of this block within ldp
+    const int NQ = Rb / 4;
+    const int64_t W = p.W, NT = p.NT;
+    const int64_t L0 = (W * b) / G, L1 = (W * (b + 1)) / G;
+    const int64_t nunits = L1 - L0;
+    // Column groups of this CTA's range.  The T block of each group the CTA starts is streamed into
+    // shared memory for the flush correction; a range that starts inside a group leaves that group
+    // to the CTA before it (its last arriver in practice), and reads T from global memory in the
+    // rare case that it finalises it.
+    const int64_t gfirst = (nunits > 0) ? L0 / NT : 0, glast = (nunits > 0) ? (L1 - 1) / NT : -1;
+    const int64_t gtf0 = (L0 % NT != 0) ? gfirst + 1 : gfirst;
+
+    if (ctl->status != 0 || ctl->stop != 0) return;  // set by the initial pass, uniform
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 2);    // X part and pivot-vector part arrive separately
+            mbar_init(&empty[s], NW);
+            mbar_init(&ybar[s], 1);    // Y chunks streamed through the same buffers
+        }
+        mbar_init(tfull, 1);
+        mbar_init(svcb, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // Y-chunk geometry: NB buffers of spb ring stages, LC columns of both planes each.
+    const int spb = loop_ybuf_stages<Cfg>(RS);
+    const int NB = S / spb;
+    const int ybuf = spb * STAGE;
+    const int yplane = LC * RS;
+    const float* ysrc = p.ysb + b * 2 * p.d_max * (int64_t)RS;
+    const uint64_t pol_y = l2_policy_evict_normal();
+    const uint64_t pol_x = p.evict_first ? l2_policy_evict_first() : l2_policy_evict_normal();
+    const uint64_t pol_v = l2_policy_evict_normal();
+    const unsigned char* planes = p.planes;
+
+    bool ok = true;
+    uint32_t gen = 0, hround = 0;
+    // producer (lane 0 of warp PROD)
+    int ps = 0;
+    uint32_t pph = 0;
+    bool preuse = false;
+    int64_t npref = 0;       // units whose X part is in the ring ahead of barrier 1
+    int pf_s0 = 0;
+    uint32_t iss_par = 0, iss_mask = 0;  // parity and presence of the last issue into each stage
+    // consumers (identical copies in every consumer thread)
+    int cs = 0;
+    uint32_t cph = 0;
+    uint32_t ypar = 0, ypend = 0;  // per Y buffer: parity of the next phase, chunk in flight
+    int64_t ypre = 0;              // chunks of the coming F issued at the end of the last pass
+    uint32_t tcnt = 0;             // T blocks streamed
+    bool tf_pend = false;
+    uint32_t dcount = 0;           // column-dot chunks (parity of their partial buffer)
+
+    int64_t piv = ctl->pivot;
+    const int mode = ctl->mode;
+    const double eps_r = ctl->eps_r, eps_r22 = ctl->eps_r22, fro_tol = ctl->fro_tol;
+    double inv_prev = 0.0;   // 1 / nu_{k-1}
+    bool small_h = true;     // ||h_{k-1}|| <= 2^-36 nu_{k-1}: Y h_{k-1} in plain FP32 is exact enough
+
+    int64_t k = p.k0;
+    int32_t stop = STOP_NONE;
+    for (;; ++k) {
+        const bool deferred = k > p.k0;            // xi_{k-1} is formed in this basis
+        const int64_t ncol = deferred ? k - 1 : k; // columns of Y streamed (complete in ysb)
+        const int64_t nch = ceil_div(ncol, (int64_t)LC);
+        const bool resident = nch <= NB;           // the slice stays in the ring for O1'
+        const int64_t ytot = resident ? nch : 2 * nch;
+        const bool run_pass = k < p.d_max;
+        const uint32_t spar = (uint32_t)((k - p.k0) & 1);
+
+        // Y chunk u of a basis with ncolv streamed columns (nchv chunks) into buffer u % NB
+        auto y_issue = [&](int64_t u, int64_t ncolv, int64_t nchv) {
+            const int bf = (int)(u % NB);
+            if (tid == 0) {
+                const int64_t l0 = (u % nchv) * LC;
+                const int lc = (int)min((int64_t)LC, ncolv - l0);
+                const uint32_t bytes = (uint32_t)lc * (uint32_t)RS * 4u;
+                float* dst = stages + (size_t)bf * ybuf;
+                mbar_arrive_expect_tx(&ybar[bf], 2u * bytes);
+                bulk_g2s(dst, ysrc + l0 * RS, bytes, &ybar[bf], pol_y);
+                bulk_g2s(dst + yplane, ysrc + (p.d_max + l0) * RS, bytes, &ybar[bf], pol_y);
+            }
+            ypend |= 1u << bf;
+        };
+        auto y_wait = [&](int bf) {
+            if (ok && !mbar_wait(&ybar[bf], (ypar >> bf) & 1u)) {
+                loop_abort(ctl, p.bar, ST_ETIMEOUT);
+                ok = false;
+            }
+            ypar ^= 1u << bf;
+            ypend &= ~(1u << bf);
+        };
+
+        // ---------------- F: xi_{k-1} and v1_k in one stream over Y ----------------
+        if (warp < NW) {
+            // the pivot column's rows of this block (row tid + i NCONS in thread tid), and the
+            // first-sweep coefficients t = T(0:k, i), split with integer operations
+            double xr[MAXRPT];
+#pragma unroll
+            for (int i = 0; i < MAXRPT; ++i) {
+                const int r = tid + i * NCONS;
+                xr[i] = (r < Rb && r0 + r < p.m) ? load_x_elem(p.X, p.xt, piv * p.ldx + r0 + r) : 0.0;
+            }
+            const double* tcol = p.T + piv * p.ldt;
+            const double tlast = deferred ? __ldcg(&tcol[k - 1]) : 0.0;
+            for (int64_t l = tid; l < ncol; l += 2 * NCONS) {
+                // both loads in flight before the shared-memory stores
+                const double t0 = __ldcg(&tcol[l]);
+                const double t1 = (l + NCONS < ncol) ? __ldcg(&tcol[l + NCONS]) : 0.0;
+                split_f64_fast(t0, cbh[l], cbl[l]);
+                if (l + NCONS < ncol) split_f64_fast(t1, cbh[l + NCONS], cbl[l + NCONS]);
+            }
+            for (int64_t u = ypre; u < min((int64_t)NB, ytot); ++u) y_issue(u, ncol, nch);
+            ypre = 0;
+            named_bar(1, NCONS);  // coefficients staged
+
+            const int NSUB = (R <= NCONS) ? (NCONS / R) : 1;
+            const int q = (R <= NCONS) ? (tid / R) : 0;
+            const int rfirst = (R <= NCONS) ? (tid % R) : tid;
+            const bool active = (R <= NCONS) ? (tid < NSUB * R) : true;
+            // B: float-float sums of Y t; A: Y h_{k-1}, plain FP32 when h is small, else float-float
+            float bs[MAXRPT], bc[MAXRPT], as[MAXRPT], ac[MAXRPT];
+#pragma unroll
+            for (int i = 0; i < MAXRPT; ++i) bs[i] = bc[i] = as[i] = ac[i] = 0.f;
+            const int amode = deferred ? (small_h ? 1 : 2) : 0;
+            for (int64_t u = 0; u < nch; ++u) {
+                const int bf = (int)(u % NB);
+                y_wait(bf);
+                const float* yh = stages + (size_t)bf * ybuf;
+                const float* yl = yh + yplane;
+                const int64_t l0 = u * LC;
+                const int lc = (int)min((int64_t)LC, ncol - l0);
+                const float* ch = cbh + l0;
+                const float* cl = cbl + l0;
+                const float* hh = cah + l0;
+                const float* hl = cal + l0;
+                if (active && ok) {
+#pragma unroll
+                    for (int i = 0; i < MAXRPT; ++i) {
+                        const int r = rfirst + i * NCONS;
+                        if (r >= Rb || (R <= NCONS && i > 0)) break;
+                        if (amode == 1) {
+                            for (int l = q; l < lc; l += NSUB) {
+                                const float y0 = yh[l * RS + r], y1 = yl[l * RS + r];
+                                ff_mac2(bs[i], bc[i], y0, y1, ch[l], cl[l]);
+                                as[i] = __fmaf_rn(y0, hh[l], as[i]);
+                            }
+                        } else if (amode == 2) {
+                            for (int l = q; l < lc; l += NSUB) {
+                                const float y0 = yh[l * RS + r], y1 = yl[l * RS + r];
+                                ff_mac2(bs[i], bc[i], y0, y1, ch[l], cl[l]);
+                                ff_mac2(as[i], ac[i], y0, y1, hh[l], hl[l]);
+                            }
+                        } else {
+                            for (int l = q; l < lc; l += NSUB)
+                                ff_mac2(bs[i], bc[i], yh[l * RS + r], yl[l * RS + r], ch[l], cl[l]);
+                        }
+                    }
+                }
+                if (!resident && u + NB < ytot) {
+                    named_bar(1, NCONS);  // buffer bf consumed
+                    y_issue(u + NB, ncol, nch);
+                }
+            }
+            named_bar_arrive(2, NCONS + 32);  // F's loads are done: the producer may use HBM
+            auto fin = [&](int r, int i, double A, double B) {
+                const bool live = r < Rb && r0 + r < p.m;
+                double xs = 0.0;  // xi_{k-1} as its split copy holds it (the value every stream sees)
+                if (deferred) {
+                    const double xi = live ? (v1s[r] - A) * inv_prev : 0.0;
+                    if (live) p.Y[(r0 + r) + (k - 1) * p.ldy] = xi;
+                    float hi, lo;
+                    split_double(xi, hi, lo);
+                    p.ysb[(b * 2 + 0) * p.d_max * RS + (k - 1) * RS + r] = hi;
+                    p.ysb[(b * 2 + 1) * p.d_max * RS + (k - 1) * RS + r] = lo;
+                    xih[r] = hi;
+                    xil[r] = lo;
+                    xs = (double)hi + (double)lo;
+                }
+                const double v = live ? (xr[i] - B) - xs * tlast : 0.0;
+                v1s[r] = v;
+                split_double(v, v1h[r], v1l[r]);
+            };
+            if (R <= NCONS) {
+                if (active) {
+                    part[q * R + rfirst] = ff_to_double(bs[0], bc[0]);
+                    part[NCONS + q * R + rfirst] = (amode == 1) ? (double)as[0] : ff_to_double(as[0], ac[0]);
+                }
+                named_bar(1, NCONS);
+                if (tid < R) {
+                    double A = 0.0, B = 0.0;
+                    if (tid < Rb && ncol > 0)
+                        for (int qq = 0; qq < NSUB; ++qq) {
+                            B += part[qq * R + tid];
+                            A += part[NCONS + qq * R + tid];
+                        }
+                    fin(tid, 0, A, B);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < MAXRPT; ++i) {
+                    const int r = tid + i * NCONS;
+                    if (r >= R) break;
+                    const bool in = r < Rb && ncol > 0;
+                    fin(r, i, in ? ((amode == 1) ? (double)as[i] : ff_to_double(as[i], ac[i])) : 0.0,
+                        in ? ff_to_double(bs[i], bc[i]) : 0.0);
+                }
+            }
+            fence_proxy_async_global();  // the new column of ysb is streamed by bulk copies later
+            named_bar(1, NCONS);         // v1 and xi_{k-1} complete in shared memory
+
+            // ---------------- O1': hpart[b] = Y_b(:, 0:k)' v1 ----------------
+            // One thread per (column, row segment) of a chunk, four float-float chains over quads
+            // of rows, the segments combined in order through shared memory.
+            auto dots_chunk = [&](const float* yh, const float* yl, int64_t l0, int lc) {
+                const int nseg = max(1, min(8, NCONS / lc));
+                const int sq = (NQ + nseg - 1) / nseg;
+                float* pf = reinterpret_cast<float*>(part) + ((dcount++ & 1u) ? 2 * NCONS : 0);
+                if (tid < nseg * lc) {
+                    const int l = tid % lc, sg = tid / lc;
+                    const int q0 = sg * sq, q1 = min(NQ, q0 + sq);
+                    const float* ch = yh + l * RS;
+                    const float* cl = yl + l * RS;
+                    float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (ok)
+                        for (int qq = q0; qq < q1; ++qq) {
+                            const float4 a = *reinterpret_cast<const float4*>(ch + 4 * qq);
+                            const float4 al = *reinterpret_cast<const float4*>(cl + 4 * qq);
+                            const float4 v = *reinterpret_cast<const float4*>(v1h + 4 * qq);
+                            const float4 vl = *reinterpret_cast<const float4*>(v1l + 4 * qq);
+                            ff_mac2(s4[0], c4[0], a.x, al.x, v.x, vl.x);
+                            ff_mac2(s4[1], c4[1], a.y, al.y, v.y, vl.y);
+                            ff_mac2(s4[2], c4[2], a.z, al.z, v.z, vl.z);
+                            ff_mac2(s4[3], c4[3], a.w, al.w, v.w, vl.w);
+                        }
+                    ff_add_acc(s4[0], c4[0], s4[1], c4[1]);
+                    ff_add_acc(s4[2], c4[2], s4[3], c4[3]);
+                    ff_add_acc(s4[0], c4[0], s4[2], c4[2]);
+                    pf[2 * (sg * lc + l)] = s4[0];
+                    pf[2 * (sg * lc + l) + 1] = c4[0];
+                }
+                named_bar(1, NCONS);
+                if (tid < lc) {
+                    float s0 = pf[2 * tid], c0 = pf[2 * tid + 1];
+                    for (int sg = 1; sg < nseg; ++sg)
+                        ff_add_acc(s0, c0, pf[2 * (sg * lc + tid)], pf[2 * (sg * lc + tid) + 1]);
+                    p.hpart[b * p.d_max + l0 + tid] = ff_to_double(s0, c0);
+                }
+            };
+            if (resident) {
+                for (int64_t u = 0; u < nch; ++u) {
+                    const float* yh = stages + (size_t)(u % NB) * ybuf;
+                    dots_chunk(yh, yh + yplane, u * LC, (int)min((int64_t)LC, ncol - u * LC));
+                }
+            } else {
+                for (int64_t u = nch; u < 2 * nch; ++u) {
+                    const int bf = (int)(u % NB);
+                    y_wait(bf);
+                    const float* yh = stages + (size_t)bf * ybuf;
+                    const int64_t l0 = (u - nch) * LC;
+                    dots_chunk(yh, yh + yplane, l0, (int)min((int64_t)LC, ncol - l0));
+                    if (u + NB < ytot) y_issue(u + NB, ncol, nch);  // dots_chunk's barrier freed it
+                }
+            }
+            if (deferred) dots_chunk(xih, xil, k - 1, 1);
+            // ||v1||^2 of this block (fixed order) and the split v1 tiles of the pass: tile t holds
+            // [hi(rows_t) | lo(rows_t)] at t * 2 * MT
+            if (warp == 0) {
+                double acc = 0.0;
+                for (int r = lane; r < Rb; r += 32) acc += v1s[r] * v1s[r];
+                acc = warp_sum_double(acc);
+                if (lane == 0) p.nu2part[b] = acc;
+            }
+            for (int r = tid; r < Rb; r += NCONS) {
+                const int64_t row = r0 + r;
+                const int64_t t = row / MT;
+                const int64_t rt = min((int64_t)MT, p.ldp - t * MT);
+                const int64_t off = t * 2 * MT + (row - t * MT);
+                p.vs[off] = v1h[r];
+                p.vs[off + rt] = v1l[r];
+            }
+            fence_proxy_async_global();  // read by the pass's bulk copies
+            named_bar_arrive(3, NCONS + 32);  // every consumer is done with the ring
+        } else if (warp == PROD) {
+            named_bar(2, NCONS + 32);
+            if (lane == 0 && run_pass) {
+                // the first tiles of the pass into L2 while the orthogonalisation runs
+                int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
+                const int64_t npf = min(nunits, (int64_t)S);
+                for (int64_t i = 0; i < npf; ++i) {
+                    const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                    bulk_prefetch_l2(planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE,
+                                     (uint32_t)(C * UB) * rows);
+                    if (++t == NT) {
+                        t = 0;
+                        ++g;
+                    }
+                }
+            }
+            named_bar(3, NCONS + 32);
+            if (lane == 0 && run_pass && ok) {
+                // ... and into the ring (their pivot-vector parts follow after barrier 1)
+                npref = min(nunits, (int64_t)S);
+                pf_s0 = ps;
+                int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
+                for (int64_t i = 0; i < npref; ++i) {
+                    if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                        loop_abort(ctl, p.bar, ST_ETIMEOUT);
+                        ok = false;
+                        npref = i;
+                        break;
+                    }
+                    const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                    const uint32_t x_bytes = (uint32_t)(C * UB) * rows;
+                    mbar_arrive_expect_tx(&full[ps], x_bytes);
+                    bulk_g2s(stages + (size_t)ps * STAGE + XI,
+                             planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE, x_bytes, &full[ps], pol_x);
+                    iss_mask |= 1u << ps;
+                    iss_par = (iss_par & ~(1u << ps)) | (pph << ps);
+                    if (++ps == S) {
+                        ps = 0;
+                        pph ^= 1u;
+                        preuse = true;
+                    }
+                    if (++t == NT) {
+                        t = 0;
+                        ++g;
+                    }
+                }
+            }
+        }
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sfl[0], ctl)) break;  // barrier 1 (uniform result)
+
+        int32_t dec = STOP_NONE;
+        if (warp == SVC) {
+            // ---------------- second sweep over the grid: h, nu, the stop tests ----------------
+            double nu2 = 0.0, fs = 0.0, hh = 0.0;
+#pragma unroll 4
+            for (int64_t bb = lane; bb < G; bb += 32) nu2 += __ldcg(&p.nu2part[bb]);
+            if (k > 0) {
+                const double* gs = p.gsum + ((k - 1) & 1) * p.ngroups;
+#pragma unroll 8
+                for (int64_t gg = lane; gg < p.ngroups; gg += 32) fs += __ldcg(&gs[gg]);
+                // this CTA's share of h, k / G coefficients, summed over the CTAs in fixed order
+                const int64_t lb0 = (k * b) / G, lb1 = (k * (b + 1)) / G;
+                for (int64_t l = lb0; l < lb1; l += 4) {
+                    double a4[4] = {0.0, 0.0, 0.0, 0.0};
+                    for (int64_t bb = lane; bb < G; bb += 32)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (l + j < lb1) a4[j] += __ldcg(&p.hpart[bb * p.d_max + l + j]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) a4[j] = warp_sum_double(a4[j]);
+                    if (lane == 0)
+                        for (int j = 0; j < 4; ++j)
+                            if (l + j < lb1) p.h[l + j] = a4[j];
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p.hcnt) : "memory");
+                }
+                ++hround;
+                if (!wait_counter(p.hcnt, p.bar, (uint32_t)G * hround)) {
+                    if (lane == 0) loop_abort(ctl, p.bar, ST_ETIMEOUT);
+                    ok = false;
+                }
+                // h (every CTA, same order): ||h||^2, and its split for the corrections of this pass
+                // and the first stream of the next basis
+                for (int64_t l = lane; l < k; l += 32) {
+                    const double hv = ok ? __ldcg(&p.h[l]) : 0.0;
+                    hh += hv * hv;
+                    split_f64_fast(hv, cah[l], cal[l]);
+                }
+                hh = warp_sum_double(hh);
+            }
+            nu2 = warp_sum_double(nu2);
+            fs = warp_sum_double(fs);
+            if (lane == 0) {
+                const double nuv = sqrt(fmax(nu2 - hh, 0.0));
+                const double frol = sqrt(fmax(fs, 0.0));
+                const double xin = sqrt(__ldg(&p.xn2[piv]));
+                int32_t st = STOP_NONE;
+                if (k > 0) {
+                    if (mode == MODE_FRO_REL) {
+                        if (frol <= fro_tol) st = STOP_TOL;
+                    } else if (nuv <= eps_r) {
+                        st = STOP_TOL;
+                    }
+                }
+                if (st == STOP_NONE && k >= p.d_max) st = STOP_DMAX;
+                if (st == STOP_NONE && (nuv < eps_r22 || nuv <= kRankFloor * xin)) st = STOP_BREAK;
+                bcast[0] = nuv;
+                bcast[1] = recip_pos(nuv);
+                bcast[2] = hh;
+                vfl[6] = hh > ldexp(nuv * nuv, -58) ? 1 : 0;  // the flush corrections in float-float
+                vfl[1] = st;
+                if (b == 0) {
+                    if (k > 0) {
+                        p.err[k - 1] = nuv;
+                        ctl->err_last = nuv;
+                        ctl->fro_last = frol;
+                    }
+                    if (st == STOP_NONE) {
+                        p.pivots[k] = piv;
+                        if (p.nu_out) p.nu_out[k] = nuv;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(svcb);
+            dec = vfl[1];
+        } else if (warp == PROD) {
+            if (lane == 0 && run_pass) {
+                int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
+                int64_t issued = nunits;
+                if (ok) {
+                    // pivot-vector tiles of the prefetched units, then the remaining units
+                    int sp = pf_s0;
+                    for (int64_t i = 0; i < npref; ++i) {
+                        const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                        const uint32_t xi_bytes = 2u * rows * 4u;
+                        mbar_arrive_expect_tx(&full[sp], xi_bytes);
+                        bulk_g2s(stages + (size_t)sp * STAGE, p.vs + t * 2 * MT, xi_bytes, &full[sp], pol_v);
+                        if (++sp == S) sp = 0;
+                        if (++t == NT) {
+                            t = 0;
+                            ++g;
+                        }
+                    }
+                    for (int64_t i = npref; i < nunits; ++i) {
+                        if (mbar_try_wait(svcb, spar) && vfl[1] != STOP_NONE) {
+                            issued = i;  // the basis was rejected: stop streaming
+                            break;
+                        }
+                        if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                            loop_abort(ctl, p.bar, ST_ETIMEOUT);
+                            ok = false;
+                            issued = i;
+                            break;
+                        }
+                        const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
+                        const uint32_t xi_bytes = 2u * rows * 4u;
+                        const uint32_t x_bytes = (uint32_t)(C * UB) * rows;
+                        float* st = stages + (size_t)ps * STAGE;
+                        mbar_arrive_expect_tx(&full[ps], x_bytes);
+                        bulk_g2s(st + XI, planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE, x_bytes,
+                                 &full[ps], pol_x);
+                        mbar_arrive_expect_tx(&full[ps], xi_bytes);
+                        bulk_g2s(st, p.vs + t * 2 * MT, xi_bytes, &full[ps], pol_v);
+                        iss_mask |= 1u << ps;
+                        iss_par = (iss_par & ~(1u << ps)) | (pph << ps);
+                        if (++ps == S) {
+                            ps = 0;
+                            pph ^= 1u;
+                            preuse = true;
+                        }
+                        if (++t == NT) {
+                            t = 0;
+                            ++g;
+                        }
+                    }
+                } else {
+                    issued = npref;
+                }
+                npref = 0;
+                vfl[3] = (int)issued;
+                __threadfence_block();
+                vfl[4] = (int)(k + 1);
+            }
+            __syncwarp();
+            if (ok && !mbar_wait(svcb, spar)) {
+                if (lane == 0) loop_abort(ctl, p.bar, ST_ETIMEOUT);
+                ok = false;
+            }
+            dec = vfl[1];
+        } else {
+            // ---------------- consumers: the pass ----------------
+            bool have_dec = false;
+            auto get_dec = [&]() {  // uniform call sites; one reader, then a barrier
+                if (have_dec) return;
+                if (tid == 0) {
+                    int d = STOP_NONE;
+                    if (ok && !mbar_wait(svcb, spar)) {
+                        loop_abort(ctl, p.bar, ST_ETIMEOUT);
+                    } else {
+                        d = vfl[1];
+                    }
+                    vfl[5] = d;
+                }
+                named_bar(1, NCONS);
+                dec = vfl[5];
+                have_dec = true;
+            };
+            if (run_pass) {
+                if (k > 0 && gtf0 <= glast) {
+                    if (tid == 0) {
+                        const uint32_t bytes = (uint32_t)(k * C * 4);
+                        mbar_arrive_expect_tx(tfull, bytes);
+                        bulk_g2s(tfb, p.tf + gtf0 * p.d_max * C, bytes, tfull, pol_v);
+                    }
+                    tf_pend = true;
+                }
+                float acc_s[CPW][4], acc_c[CPW][4];
+#pragma unroll
+                for (int qq = 0; qq < CPW; ++qq)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
+                double best_e = -1.0;
+                int64_t best_j = INT64_MAX;
+                double e_old[CPW];
+#pragma unroll
+                for (int qq = 0; qq < CPW; ++qq) e_old[qq] = 0.0;
+                int gbuf = 0;
+                bool cut = false;
+                double* gsum_k = p.gsum + (k & 1) * p.ngroups;
+                int64_t g_next = L0 / NT, t_next = L0 - (L0 / NT) * NT;
+                for (int64_t u = L0; u < L1; ++u) {
+                    const int64_t g = g_next, t = t_next;
+                    const int s = cs;
+                    const uint32_t ph = cph;
+                    if (++cs == S) {
+                        cs = 0;
+                        cph ^= 1u;
+                    }
+                    if (++t_next == NT) {
+                        t_next = 0;
+                        ++g_next;
+                    }
+                    // Wait for the unit, unless the producer stopped issuing before it (a basis the
+                    // service warp rejected: the producer sees the decision before the consumers
+                    // reach a finalised group).  Every consumer thread reaches the same verdict: the
+                    // unit either arrives or is known never to be issued.
+                    bool got = true;
+                    if (ok && !mbar_try_wait(&full[s], ph)) {
+                        const uint64_t t0 = globaltimer_ns();
+                        while (true) {
+                            if (mbar_try_wait(&full[s], ph)) break;
+                            if (vfl[4] == (int)(k + 1) && (u - L0) >= (int64_t)vfl[3]) {
+                                got = false;
+                                break;
+                            }
+                            if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                                loop_abort(ctl, p.bar, ST_ETIMEOUT);
+                                ok = false;
+                                break;
+                            }
+                        }
+                    }
+                    if (!got) {
+                        // nothing further is in flight; the stage sequence stays aligned with the
+                        // producer's, which issued nothing from here
+                        cs = s;
+                        cph = ph;
+                        break;
+                    }
+                    if (cut) {
+                        // the basis was rejected: drain without arithmetic
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&empty[s]);
+                        continue;
+                    }
+                    const int64_t c0 = g * C;
+                    const int ncols = (int)min((int64_t)C, p.n - c0);
+                    if (lane == 0 && (t == 0 || u == L0)) {
+#pragma unroll
+                        for (int qq = 0; qq < CPW; ++qq) {
+                            const int cw = warp * CPW + qq;
+                            if (cw < ncols) e_old[qq] = __ldcg(&p.e[c0 + cw]);
+                        }
+                    }
+                    const int rows = (int)min((int64_t)MT, p.ldp - t * MT);
+                    if (ok) {
+                        const float* st = stages + (size_t)s * STAGE;
+                        if constexpr (XT == 2) {
+                            if (rows == MT)
+                                consume_tile_bf16<CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
+                            else
+                                consume_tile_bf16<CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c);
+                        } else {
+                            if (rows == MT)
+                                consume_tile<Cfg::PL, CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
+                            else
+                                consume_tile<Cfg::PL, CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c);
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                    if (t != NT - 1 && u != L1 - 1) continue;
+
+                    // ---------------- end of this CTA's share of column group g ----------------
+                    double tot[CPW];
+#pragma unroll
+                    for (int qq = 0; qq < CPW; ++qq) {
+                        float sq = acc_s[qq][0], cq = acc_c[qq][0];
+#pragma unroll
+                        for (int e = 1; e < 4; ++e) ff_add(sq, cq, acc_s[qq][e], acc_c[qq][e]);
+                        warp_sum_ff(sq, cq);
+                        tot[qq] = ff_to_double(sq, cq);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
+                    }
+                    const bool tf_here = k > 0 && g >= gtf0;  // this group's T block was streamed
+                    if (tf_here) {
+                        if (ok && !mbar_wait(tfull, tcnt & 1u)) {
+                            loop_abort(ctl, p.bar, ST_ETIMEOUT);
+                            ok = false;
+                        }
+                        ++tcnt;
+                        tf_pend = false;
+                    }
+                    const bool whole = (g * NT >= L0) && ((g + 1) * NT <= L1);
+                    bool fin_here = true;
+                    if (!whole) {
+                        // a group split between CTAs: publish this share; the last to arrive sums
+                        // the shares in CTA order
+                        const int64_t bfirst = unit_owner(g * NT, W, G);
+                        const int64_t blast = unit_owner(g * NT + NT - 1, W, G);
+                        const uint32_t ncontrib = (uint32_t)(blast - bfirst + 1);
+                        const int64_t slot = b - bfirst;
+                        if (lane == 0) {
+#pragma unroll
+                            for (int qq = 0; qq < CPW; ++qq) {
+                                const int cw = warp * CPW + qq;
+                                if (cw < ncols) p.gslot[(g * p.KMAX + slot) * C + cw] = tot[qq];
+                            }
+                            __threadfence();
+                        }
+                        named_bar(1, NCONS);
+                        if (tid == 0) vfl[2] = (atomicAdd(&p.gcnt[g], 1u) == ncontrib - 1);
+                        named_bar(1, NCONS);
+                        fin_here = vfl[2] != 0;
+                        if (fin_here) {
+                            __threadfence();
+                            if (lane == 0) {
+#pragma unroll
+                                for (int qq = 0; qq < CPW; ++qq) {
+                                    const int cw = warp * CPW + qq;
+                                    if (cw < ncols) {
+                                        double acc = 0.0;
+                                        for (uint32_t sl = 0; sl < ncontrib; ++sl)
+                                            acc += __ldcg(&p.gslot[(g * p.KMAX + sl) * C + cw]);
+                                        tot[qq] = acc;
+                                    }
+                                }
+                            }
+                            if (tid == 0) p.gcnt[g] = 0;
+                        }
+                    }
+                    if (fin_here) {
+                        get_dec();
+                        if (dec != STOP_NONE) {
+                            cut = true;
+                            continue;
+                        }
+                        const double inv_nu = bcast[1];
+                        // correction -h' T(0:k, j) of the columns' dot products
+                        if (k > 0 && vfl[6]) {
+                            // ||h|| / nu > 2^-29: FP32 would leave more than FP64 rounding in T(k, j),
+                            // and T(:, i) is the next bases' first sweep.  Float-float products of the
+                            // split h with T read in FP64, lanes 0-15 of a warp on its first column,
+                            // 16-31 on its second, summed over the half-warp in a fixed tree.
+                            static_assert(CPW == 2, "one half-warp per column");
+                            const int cw = warp * CPW + (lane >> 4);
+                            float s = 0.f, cc = 0.f;
+                            if (cw < ncols) {
+                                const double* tcolj = p.T + (c0 + cw) * p.ldt;
+                                for (int64_t l = lane & 15; l < k; l += 16) {
+                                    float th, tl;
+                                    split_f64_fast(__ldcg(&tcolj[l]), th, tl);
+                                    ff_mac2(s, cc, th, tl, cah[l], cal[l]);
+                                }
+                            }
+#pragma unroll
+                            for (int o = 8; o > 0; o >>= 1) {
+                                const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+                                const float c2 = __shfl_xor_sync(0xffffffffu, cc, o);
+                                ff_add(s, cc, s2, c2);
+                            }
+                            const double cr = ff_to_double(s, cc);
+                            const double cr1 = __shfl_sync(0xffffffffu, cr, 16);
+                            if (lane == 0) {
+                                tot[0] -= cr;
+                                tot[1] -= cr1;
+                            }
+                        } else if (k > 0) {
+                            // FP32: the term is ||h|| / nu <= 2^-29 relative to the column's norm
+                            const int c = tid % C, ls = tid / C;
+                            float sacc = 0.f;
+                            if (tf_here) {
+                                for (int64_t l = ls; l < k; l += NLS) sacc = __fmaf_rn(cah[l], tfb[l * C + c], sacc);
+                            } else {
+                                const float* tg = p.tf + g * p.d_max * C;
+                                for (int64_t l = ls; l < k; l += NLS) sacc = __fmaf_rn(cah[l], __ldcg(&tg[l * C + c]), sacc);
+                            }
+                            sacc = __fadd_rn(sacc, __shfl_xor_sync(0xffffffffu, sacc, 16));
+                            if (lane < 16) corr[warp * C + lane] = sacc;
+                            named_bar(1, NCONS);
+                            if (lane == 0) {
+#pragma unroll
+                                for (int qq = 0; qq < CPW; ++qq) {
+                                    const int cw = warp * CPW + qq;
+                                    float cr = 0.f;
+#pragma unroll
+                                    for (int w = 0; w < NW; ++w) cr = __fadd_rn(cr, corr[w * C + cw]);
+                                    tot[qq] -= (double)cr;
+                                }
+                            }
+                        }
+                        if (lane == 0) {
+#pragma unroll
+                            for (int qq = 0; qq < CPW; ++qq) {
+                                const int cw = warp * CPW + qq;
+                                if (cw < ncols) {
+                                    const int64_t j = c0 + cw;
+                                    const double cj = tot[qq] * inv_nu;
+                                    p.T[j * p.ldt + k] = cj;
+                                    p.tf[(g * p.d_max + k) * C + cw] = __double2float_rn(cj);
+                                    const double en = (j == piv) ? 0.0 : fmax(e_old[qq] - cj * cj, 0.0);
+                                    p.e[j] = en;
+                                    grp_e[gbuf * C + cw] = en;
+                                    if (better(en, j, best_e, best_j)) {
+                                        best_e = en;
+                                        best_j = j;
+                                    }
+                                }
+                            }
+                            fence_proxy_async_global();  // this row of the FP32 T is streamed later
+                        }
+                        // one barrier per group: thread 0 sums this buffer while the other warps move
+                        // on; it is written again two groups later, after thread 0 passed the next
+                        // barrier
+                        named_bar(1, NCONS);
+                        if (tid == 0) {
+                            double sacc = 0.0;
+                            for (int cw = 0; cw < ncols; ++cw) sacc += grp_e[gbuf * C + cw];
+                            gsum_k[g] = sacc;
+                        }
+                        gbuf ^= 1;
+                    }
+                    // the next group's T block (the buffer was read before the last barrier)
+                    if (k > 0 && g >= gtf0 && g + 1 <= glast) {
+                        if (tid == 0) {
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            const uint32_t bytes = (uint32_t)(k * C * 4);
+                            mbar_arrive_expect_tx(tfull, bytes);
+                            bulk_g2s(tfb, p.tf + (g + 1) * p.d_max * C, bytes, tfull, pol_v);
+                        }
+                        tf_pend = true;
+                    }
+                }
+                get_dec();  // a CTA that finalised no group learns the decision here
+                if (dec == STOP_NONE) {
+                    if (lane == 0) {
+                        red_e[warp] = best_e;
+                        red_j[warp] = best_j;
+                    }
+                    named_bar(1, NCONS);
+                    if (tid == 0) {
+                        double be = -1.0;
+                        int64_t bj = INT64_MAX;
+                        for (int w = 0; w < NW; ++w)
+                            if (better(red_e[w], red_j[w], be, bj)) {
+                                be = red_e[w];
+                                bj = red_j[w];
+                            }
+                        p.pbest_e[b] = be;
+                        p.pbest_j[b] = bj;
+                    }
+                }
+            } else {
+                get_dec();
+            }
+            if (dec == STOP_NONE && ok) {
+                // the Y chunks of the next basis's first stream (columns 0..k-1 are complete; column
+                // k is formed there) into the ring, which every consumer has left
+                const int64_t ncol2 = k, nch2 = ceil_div(ncol2, (int64_t)LC);
+                const int64_t tot2 = (nch2 <= NB) ? nch2 : 2 * nch2;
+                ypre = min((int64_t)NB, tot2);
+                for (int64_t u = 0; u < ypre; ++u) y_issue(u, ncol2, nch2);
+            }
+        }
+        // every role leaves the loop together: the decision as the service warp wrote it, read by
+        // all threads after one CTA barrier (a role's own copy can differ only after a timeout)
+        __syncthreads();
+        dec = vfl[1];
+        if (dec != STOP_NONE) {
+            stop = dec;
+            break;
+        }
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sfl[0], ctl)) break;  // barrier 2 (uniform result)
+
+        // ---------------- A: argmax over CTAs ----------------
+        if (warp == 0) {
+            double be = -1.0;
+            int64_t bj = INT64_MAX;
+#pragma unroll 8
+            for (int64_t cb = lane; cb < G; cb += 32) {
+                const double ce = __ldcg(&p.pbest_e[cb]);
+                const int64_t cj = __ldcg(reinterpret_cast<const long long*>(&p.pbest_j[cb]));
+                if (better(ce, cj, be, bj)) {
+                    be = ce;
+                    bj = cj;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double oe = __shfl_down_sync(0xffffffffu, be, o);
+                const int64_t oj = __shfl_down_sync(0xffffffffu, bj, o);
+                if (better(oe, oj, be, bj)) {
+                    be = oe;
+                    bj = oj;
+                }
+            }
+            if (lane == 0) red_j[0] = (bj >= 0 && bj < p.n) ? bj : piv;
+        }
+        __syncthreads();
+        piv = red_j[0];
+        {
+            const double nuv = bcast[0];
+            inv_prev = bcast[1];
+            small_h = bcast[2] <= ldexp(nuv * nuv, -72);
+        }
+        if (b == 0 && tid == 0) {
+            ctl->d = k + 1;
+            ctl->pivot = piv;
+        }
+        __syncthreads();
+    }
+
+    // ---------------- leave: no bulk copy may still be writing this CTA's shared memory ----------------
+    if (warp == PROD && lane == 0) {
+        // X parts prefetched ahead of a barrier that failed: complete those phases' second arrival
+        for (int64_t i = 0; i < npref; ++i) mbar_arrive(&full[(pf_s0 + (int)i) % S]);
+        for (int s = 0; s < S; ++s)
+            if ((iss_mask >> s) & 1u)
+                if (!mbar_wait(&full[s], (iss_par >> s) & 1u)) {
+                    raise_status(ctl, ST_ETIMEOUT);
+                    break;
+                }
+    }
+    if (warp < NW && tid == 0) {
+        for (int bf = 0; bf < NB; ++bf)
+            if ((ypend >> bf) & 1u)
+                if (!mbar_wait(&ybar[bf], (ypar >> bf) & 1u)) raise_status(ctl, ST_ETIMEOUT);
+        if (tf_pend && !mbar_wait(tfull, tcnt & 1u)) raise_status(ctl, ST_ETIMEOUT);
+    }
+    if (b == 0 && tid == 0 && stop != STOP_NONE) {
+        ctl->stop = stop;
+        ctl->d = k;
+        ctl->pivot = piv;
+    }
+}
+
+size_t defer_smem_bytes(int xt, int R, int KC) {
+    if (xt == 0) return defer_smem_layout<TileCfg<0>>(R, KC).total;
+    if (xt == 1) return defer_smem_layout<TileCfg<1>>(R, KC).total;
+    if (xt == 2) return defer_smem_layout<TileCfg<2>>(R, KC).total;
+    return 0;
+}
+
+int defer_chunk_cols(int xt, int RS) {
+    if (xt == 0) return loop_chunk_cols<TileCfg<0>>(RS);
+    if (xt == 1) return loop_chunk_cols<TileCfg<1>>(RS);
+    if (xt == 2) return loop_chunk_cols<TileCfg<2>>(RS);
+    return 0;
+}
+
+static const void* defer_fn(int xt) {
+    return (xt == 0) ? (const void*)defer_kernel<0> : (xt == 1) ? (const void*)defer_kernel<1>
+                                                                : (const void*)defer_kernel<2>;
+}
+
+cudaError_t defer_kernel_setup(int max_smem) {
+    cudaError_t e = cudaSuccess;
+    for (int xt = 0; xt < 3 && e == cudaSuccess; ++xt)
+        e = cudaFuncSetAttribute(defer_fn(xt), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    return e;
+}
+
+cudaError_t launch_defer(const Work& w, const void* X, double* Y, int64_t ldy, double* T, int64_t ldt,
+                         int64_t* pivots, double* err, double* nu_out, int64_t k0, cudaStream_t st) {
+    DeferParams p;
+    p.m = w.m;
+    p.n = w.n;
+    p.ldp = w.ldp;
+    p.ldx = w.ldx;
+    p.ldt = ldt;
+    p.ldy = ldy;
+    p.d_max = w.d_max;
+    p.k0 = k0;
+    p.xt = w.xt;
+    p.planes = static_cast<const unsigned char*>(w.planes);
+    p.group_stride = w.group_stride;
+    p.tile_stride = w.tile_stride;
+    p.NT = w.NT;
+    p.ngroups = w.ngroups;
+    p.W = w.W;
+    p.KMAX = w.KMAX;
+    p.evict_first = w.evict_first;
+    p.X = X;
+    p.Y = Y;
+    p.T = T;
+    p.pivots = pivots;
+    p.err = err;
+    p.nu_out = nu_out;
+    p.ctl = w.ctl;
+    p.bar = &w.ctl->bar[0];
+    p.hcnt = &w.ctl->bar[1];
+    p.e = w.e;
+    p.xn2 = w.xn2;
+    p.ysb = w.ysb;
+    p.vs = w.v2s;
+    p.tf = w.tf;
+    p.hpart = w.hpart;
+    p.h = w.h;
+    p.nu2part = w.nu2part;
+    p.pbest_e = w.pbest_e;
+    p.pbest_j = w.pbest_j;
+    p.gcnt = w.gcnt;
+    p.gslot = w.gslot;
+    p.gsum = w.gsum;
+    p.R = w.R;
+    p.RS = w.RS;
+    p.LC = w.LC;
+    p.KC = w.KC;
+    void* args[] = {&p};
+    const int threads =
+        32 + ((w.xt == 0) ? TileCfg<0>::THREADS : (w.xt == 1) ? TileCfg<1>::THREADS : TileCfg<2>::THREADS);
+    return cudaLaunchCooperativeKernel(defer_fn(w.xt), dim3((unsigned)w.G_loop), dim3((unsigned)threads), args,
+                                       w.loop_smem, st);
+}
+
+}  // namespace rbd

@@ -154,21 +154,28 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
     lo = __double2float_rn(x - (double)hi);
 }
 
-// Split an FP64 value into FP32 hi + lo with integer operations only (no FP64 pipe):
-// hi keeps the sign, exponent and leading 24 significant bits (truncated); lo is the exact
-// remainder r * 2^(E-1075) (r < 2^29) rounded to 24 bits.  |x - hi - lo| <= 2^-48 |x|.
-// Values outside 2^-74 <= |x| < 2^127 take the FP64 conversion path.
+// Split an FP64 value into FP32 hi + lo with integer operations only (no FP64 pipe): hi is x
+// rounded to nearest at 24 significant bits (a carry out of the significand moves into the
+// exponent), lo the signed remainder, an integer of at most 2^28 units of x's last place, rounded
+// to 24 bits by the integer-to-float conversion.  |lo| <= 2^-24 |x| and |x - hi - lo| <= 2^-48 |x|,
+// as for split_double; the small |lo| matters where float-float products drop lo * lo.  Values
+// outside 2^-74 <= |x| < 2^127 take the FP64 conversion path.
 __device__ __forceinline__ void split_f64_fast(double x, float& hi, float& lo) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+    const uint32_t bh = (uint32_t)(b >> 32);
     const int E = (int)((bh >> 20) & 0x7ffu);
     if (E >= 949 && E <= 1149) {
+        const uint32_t r29 = (uint32_t)b & 0x1fffffffu;  // the significand's low 29 bits
+        const bool up = r29 >= 0x10000000u;
+        const unsigned long long hb = (b & ~0x1fffffffull) + (up ? 0x20000000ull : 0ull);
+        const uint32_t hbh = (uint32_t)(hb >> 32), hbl = (uint32_t)hb;
+        const int Eh = (int)((hbh >> 20) & 0x7ffu);
         const uint32_t sign = bh & 0x80000000u;
-        const uint32_t mant23 = ((bh & 0xfffffu) << 3) | (bl >> 29);
-        hi = __uint_as_float(sign | ((uint32_t)(E - 896) << 23) | mant23);
-        const uint32_t r = bl & 0x1fffffffu;
-        const float scale = __uint_as_float((uint32_t)(E - 948) << 23);  // 2^(E-1075)
-        lo = __uint_as_float(__float_as_uint(__fmul_rn(__uint2float_rn(r), scale)) | sign);
+        hi = __uint_as_float(sign | ((uint32_t)(Eh - 896) << 23) | ((hbh & 0xfffffu) << 3) | (hbl >> 29));
+        const int rem = (int)r29 - (up ? 0x20000000 : 0);                // x - hi in units of 2^(E-1075)
+        const float scale = __uint_as_float((uint32_t)(E - 948) << 23);  // 2^(E-1075), exact
+        const float lv = __fmul_rn(__int2float_rn(rem), scale);
+        lo = sign ? -lv : lv;
     } else {
         split_double(x, hi, lo);
     }

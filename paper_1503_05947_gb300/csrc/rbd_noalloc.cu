@@ -9,9 +9,11 @@
 // as this translation unit's module is loaded on a device, and calls no allocating routine:
 // no cudaMalloc / cudaMallocAsync / cudaFree, no host-pinned or mapped buffer, no CUDA events.
 //
-// Setup: the first call on a device (with that device current) sets the kernel attributes and
-// looks up the array's device address with cudaGetSymbolAddress; later calls on that device
-// reuse what was recorded.  Because the array is one per device and per process, calls that
+// Setup: the first call on a device (with that device current) sets the kernel attributes (the
+// same per-device setup as rbd_compress, device_state in rbd_abi.cu) and looks up the array's
+// device address with cudaGetSymbolAddress; later calls on that device reuse what was recorded.
+// The argument rules and the choice of path are rbd_compress's own (validate, plan_work), so the
+// two entry points cannot drift apart.  Because the array is one per device and per process, calls that
 // overlap on the same device -- from several host threads, or on several streams -- race on
 // it and corrupt each other's results: callers serialise them.
 #include <cstring>
@@ -29,76 +31,26 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[RBD_NOALLOC_SCR
 
 namespace {
 
-struct NoallocDevice {
-    bool ready = false;
-    int num_sms = 0;
-    int pass_ctas_per_sm[3] = {1, 1, 1};
-    int loop_max_smem = 0;
-    void* scratch = nullptr;
-};
-
 std::mutex g_na_mu;
-NoallocDevice g_na_dev[64];
+void* g_na_scratch[64];
 
-bool stepwise_forced() {
-    const char* v = getenv("RBD_STEPWISE");
-    return v && v[0] && v[0] != '0';
-}
-
-// One-time setup of the current device: SM count, kernel attributes, scratch address.
-cudaError_t noalloc_device(NoallocDevice& out) {
+// The device address of g_noalloc_scratch on the current device (looked up once per device;
+// in host code the array's name is only a host-side stand-in for it).
+cudaError_t noalloc_scratch(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_na_mu);
-    NoallocDevice& s = g_na_dev[dev];
-    if (!s.ready) {
-        e = cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        e = pass_kernel_setup(s.pass_ctas_per_sm);
-        if (e != cudaSuccess) return e;
-        int coop = 0, optin = 0;
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        s.loop_max_smem = 0;
-        if (coop && optin > 0) {
-            if (loop_kernel_setup(optin) == cudaSuccess)
-                s.loop_max_smem = optin;
-            else
-                cudaGetLastError();
-        }
+    if (!g_na_scratch[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         if (p == nullptr || ((uintptr_t)p & 255u) != 0) return cudaErrorInvalidSymbol;
-        s.scratch = p;
-        s.ready = true;
+        g_na_scratch[dev] = p;
     }
-    out = s;
-    if (stepwise_forced()) out.loop_max_smem = 0;
+    *out = g_na_scratch[dev];
     return cudaSuccess;
-}
-
-rbd_status map_err(cudaError_t e) {
-    if (e == cudaSuccess) return RBD_OK;
-    if (e == cudaErrorMemoryAllocation) return RBD_ENOMEM;
-    return RBD_ECUDA;
-}
-
-// The argument rules of rbd_compress.
-rbd_status check_args(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol,
-                      rbd_tol_mode mode, int64_t d_max, int64_t start, const double* Y, int64_t ldy,
-                      const double* T, int64_t ldt, const int64_t* pivots, const double* err) {
-    if (!X || !Y || !T || !pivots || !err) return RBD_EINVAL;
-    if (xt != RBD_F64 && xt != RBD_F32 && xt != RBD_BF16) return RBD_EINVAL;
-    if (m < 1 || n < 1 || ldx < m || ldy < m || d_max < 1 || ldt < d_max) return RBD_EINVAL;
-    if (d_max > m || d_max > n) return RBD_EINVAL;
-    if (start < 0 || start >= n) return RBD_EINVAL;
-    if (!(tol >= 0.0) || tol == __builtin_inf()) return RBD_EINVAL;
-    if (mode != RBD_TOL_MAXCOL_ABS && mode != RBD_TOL_MAXCOL_REL && mode != RBD_TOL_FRO_REL) return RBD_EINVAL;
-    if (m > (int64_t(1) << 40) || n > (int64_t(1) << 40)) return RBD_EUNSUPPORTED;
-    return RBD_OK;
 }
 
 }  // namespace
@@ -110,13 +62,15 @@ extern "C" rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t 
                                            double tol, rbd_tol_mode mode, int64_t d_max, int64_t start,
                                            double* Y, int64_t ldy, double* T, int64_t ldt, int64_t* pivots,
                                            double* err, double* nu, void* stream, rbd_result* result) {
-    rbd_status v = check_args(X, xt, m, n, ldx, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err);
+    rbd_status v = validate(X, xt, m, n, ldx, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err);
     if (v != RBD_OK) return v;
-    NoallocDevice ds;
-    cudaError_t ce = noalloc_device(ds);
+    DeviceState ds;
+    void* scratch = nullptr;
+    cudaError_t ce = device_state(ds);
+    if (ce == cudaSuccess) ce = noalloc_scratch(&scratch);
     if (ce != cudaSuccess) {
         cudaGetLastError();
-        return map_err(ce);
+        return map_cuda(ce);
     }
     Work w;
     if (!plan_work(w, m, n, ldx, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem))
@@ -124,19 +78,20 @@ extern "C" rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t 
     if (xt == RBD_BF16 && !w.use_loop) return RBD_EUNSUPPORTED;
     // the problem's workspace must fit the fixed array
     if (w.total_bytes > (size_t)RBD_NOALLOC_SCRATCH_BYTES) return RBD_ENOMEM;
-    carve_work(w, ds.scratch);
+    carve_work(w, scratch);
     cudaStream_t st = (cudaStream_t)stream;
 
     // the control block and the last-arriver counters start at zero
     int32_t launches = 0;
-    ce = cudaMemsetAsync(ds.scratch, 0, w.zero_bytes, st);
+    ce = cudaMemsetAsync(scratch, 0, w.zero_bytes, st);
     if (ce == cudaSuccess) {
         ce = launch_init(w, X, tol, (int)mode, start, st);
         ++launches;
     }
     if (w.use_loop) {
         if (ce == cudaSuccess) {
-            ce = launch_loop(w, X, Y, ldy, T, ldt, pivots, err, nu, 0, st);
+            ce = w.use_defer ? launch_defer(w, X, Y, ldy, T, ldt, pivots, err, nu, 0, st)
+                             : launch_loop(w, X, Y, ldy, T, ldt, pivots, err, nu, 0, st);
             ++launches;
         }
     } else {
@@ -168,7 +123,7 @@ extern "C" rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t 
     if (ce == cudaSuccess) ce = se;
     if (ce != cudaSuccess) {
         cudaGetLastError();
-        return map_err(ce);
+        return map_cuda(ce);
     }
     rbd_status rs = (hctl.status != ST_OK) ? (rbd_status)hctl.status : RBD_OK;
     if (result) {

@@ -7,6 +7,8 @@
 //   resume_state_kernel     e_j = ||x_j||^2 downdated by T(l, j)^2 for l = 0..d0-1 (Eq. (evalerr),
 //                           A = I; the pivot column of step l is set to 0 there), and the
 //                           per-group sums of e_j for the Frobenius residual
+//                           (and, for the two-barrier loop kernel, T(0:d0, :) in FP32 in the
+//                           group-blocked layout its flush corrections stream)
 //   resume_y_kernel         the split FP32 copy of Y the Gram-Schmidt GEMVs stream
 //   resume_finalize_kernel  the Frobenius residual (the order of the path that continues), the
 //                           next pivot and d in the control block
@@ -28,7 +30,9 @@ struct ResumeParams {
     int C;
     double* e;
     const double* xn2;
-    double* gsum;
+    double* gsum;         // the group sums the continuing path reads first (a parity copy on the
+                          // two-barrier path)
+    float* tf;            // two-barrier path: T(0:d0, :) in FP32, group-blocked; else nullptr
     int use_loop;
     float* ysb;   // persistent kernel: [G][2][d_max][RS]
     int R, RS, G_loop;
@@ -51,6 +55,7 @@ __global__ void __launch_bounds__(256) resume_state_kernel(ResumeParams p) {
             for (int64_t l = 0; l < p.k0; ++l) {
                 const double c = p.T[j * p.ldt + l];
                 e = (j == p.piv[l]) ? 0.0 : fmax(e - c * c, 0.0);
+                if (p.tf) p.tf[(g * p.d_max + l) * p.C + lane] = __double2float_rn(c);
             }
             p.e[j] = e;
         }
@@ -123,7 +128,9 @@ cudaError_t launch_resume(const Work& w, const double* Y, int64_t ldy, const dou
     p.C = w.C;
     p.e = w.e;
     p.xn2 = w.xn2;
-    p.gsum = w.gsum;
+    // the two-barrier kernel's service warps read the sums of basis k0 - 1 from copy (k0 - 1) & 1
+    p.gsum = w.use_defer ? w.gsum + ((k0 - 1) & 1) * w.ngroups : w.gsum;
+    p.tf = w.use_defer ? w.tf : nullptr;
     p.use_loop = w.use_loop;
     p.ysb = w.ysb;
     p.R = w.R;

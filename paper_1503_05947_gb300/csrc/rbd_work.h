@@ -23,7 +23,10 @@
 //   zs       loop path, A-norm form: z = (I - Y Y') (w o v2) split like v2s (the second pivot vector)
 //   rb_cnt, lb_cnt, gcnt   last-arriver counters (zero at rest)
 //   gslot    per-column-group partial dot products (2 x ngroups x KMAX x C: xi, then z)
-//   gsum     per-column-group sums of e_j (ngroups)
+//   gsum     per-column-group sums of e_j (ngroups; two copies by parity of the basis on the
+//            two-barrier loop path, whose service warps read one while the pass writes the other)
+//   tf       two-barrier loop path: T in FP32, group-blocked [ngroups][d_max][C], streamed per group
+//            for the correction of the pass's dot products
 //   pbest_e/j  per-CTA argmax candidates of the fused pass (G)
 #pragma once
 
@@ -31,6 +34,8 @@
 #include <stdint.h>
 
 #include <cuda_runtime.h>
+
+#include "rbd.h"
 
 // Fused-pass tile shape (compile-time; the defaults are the tuned GB300 values).
 #ifndef RBD_PASS_NW
@@ -150,6 +155,8 @@ struct Work {
     int RS;                 // column stride of a CTA's Y slice: R, or R + 4, so that RS = 4 mod 8
     int LC;                 // Y columns per streamed chunk
     size_t loop_smem;       // dynamic shared memory bytes
+    int use_defer;          // A = I: the two-barrier loop kernel (rbd_defer.cu) instead of rbd_loop.cu's
+    int KC;                 // d_max rounded up to 4 (coefficient and T-block rows in shared memory)
     // regions
     Ctl* ctl;
     void* planes;
@@ -163,7 +170,8 @@ struct Work {
     double *hpart, *h;
     double* nu2part;
     uint32_t *rb_cnt, *lb_cnt, *gcnt;
-    double *gslot, *gsum;
+    double *gslot, *gsum;   // gsum: 2 x ngroups (by parity of the basis) on the two-barrier path
+    float* tf;              // two-barrier path: T in FP32, [ngroups][d_max][C]
     double* pbest_e;
     int64_t* pbest_j;
     // bytes of the zero-at-rest prefix (ctl + counters) to clear at call start
@@ -180,6 +188,23 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
                int pass_ctas_per_sm, int loop_max_smem, int wt = 0);
 // Carve the regions of `w` out of `base` (at least w.total_bytes, 256-byte aligned).
 void carve_work(Work& w, void* base);
+
+// Per-device state: SM count and the one-time kernel attribute setup (cached per device; the
+// first call on a device, with that device current, does the setup).  RBD_STEPWISE=1 reports no
+// loop-kernel shared memory, which selects the stepwise path.
+struct DeviceState {
+    int num_sms = 0;
+    int pass_ctas_per_sm[3] = {1, 1, 1};
+    int loop_max_smem = 0;  // 0: the persistent loop kernels are not used on this device
+    bool ready = false;
+};
+cudaError_t device_state(DeviceState& out);
+// cudaError_t -> rbd_status (allocation failures are RBD_ENOMEM, every other error RBD_ECUDA).
+rbd_status map_cuda(cudaError_t e);
+// The argument rules of rbd_compress (and of every entry point that takes its arguments).
+rbd_status validate(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx, double tol, rbd_tol_mode mode,
+                    int64_t d_max, int64_t start, const double* Y, int64_t ldy, const double* T, int64_t ldt,
+                    const int64_t* pivots, const double* err);
 
 // ---- launchers (each returns the cudaError_t of its launch) ----
 // With w.wts set: e_j = ||x_j||_A^2 (xn2 stays Euclidean) and the tolerance scales in A-norms.
@@ -215,5 +240,12 @@ int loop_chunk_cols_for(int xt, int wt, int R);
 cudaError_t loop_kernel_setup(int max_smem);
 cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, double* T, int64_t ldt,
                         int64_t* pivots, double* err, double* nu_out, int64_t k0, cudaStream_t st);
+// The two-barrier persistent loop kernel (A = I): shared-memory bytes, Y columns per streamed chunk,
+// one-time attribute setup and the cooperative launch.
+size_t defer_smem_bytes(int xt, int R, int KC);
+int defer_chunk_cols(int xt, int RS);
+cudaError_t defer_kernel_setup(int max_smem);
+cudaError_t launch_defer(const Work& w, const void* X, double* Y, int64_t ldy, double* T, int64_t ldt,
+                         int64_t* pivots, double* err, double* nu_out, int64_t k0, cudaStream_t st);
 
 }  // namespace rbd

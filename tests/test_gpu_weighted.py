@@ -95,15 +95,26 @@ def test_weighted_pins_on_cuda_path(rbd, pin):
     pin(gpu_compress)
 
 
-def test_unit_weights_equal_unweighted_path(rbd):
+def test_unit_weights_equal_unweighted_path(rbd, monkeypatch):
     Xn = gen.decay_matrix_c1(seed=2, noise_sigma=1e-5, m=1500, n=700)
     X = to_device(Xn)
+    w1 = torch.ones(1500, dtype=torch.float64, device="cuda")
+    b = rbd.compress(X, 1e-6, 80, tol_mode="maxcol_abs", weights=w1)
+    # the four-barrier kernel of the unweighted form takes the same operations for the basis and
+    # T as the A-norm form; the indicator update differs by rounding only
+    monkeypatch.setenv("RBD_LOOP_CLASSIC", "1")
     a = rbd.compress(X, 1e-6, 80, tol_mode="maxcol_abs")
-    b = rbd.compress(X, 1e-6, 80, tol_mode="maxcol_abs", weights=torch.ones(1500, dtype=torch.float64, device="cuda"))
+    monkeypatch.delenv("RBD_LOOP_CLASSIC")
     assert a.d == b.d and torch.equal(a.pivots, b.pivots)
-    # the basis and T take the same operations; the indicator update differs by rounding only
     assert torch.equal(a.Y, b.Y) and torch.equal(a.T, b.T) and torch.equal(a.nu, b.nu)
     assert torch.allclose(a.err, b.err, rtol=1e-14, atol=0.0)
+    # the default (two-barrier) unweighted kernel: the same pivots, Y and T at the parity bar
+    c = rbd.compress(X, 1e-6, 80, tol_mode="maxcol_abs")
+    assert c.d == b.d and torch.equal(c.pivots, b.pivots)
+    scale = np.linalg.norm(Xn, axis=0)
+    assert np.linalg.norm(to_numpy(c.Y) - to_numpy(b.Y), axis=0).max() <= 1e-10
+    assert (np.abs(to_numpy(c.T) - to_numpy(b.T)) / scale[None, :]).max() <= 1e-10
+    assert (c.err - b.err).abs().max().item() <= 1e-10 * scale.max()
 
 
 @pytest.mark.parametrize("bad", [0.0, -1.0, float("nan"), float("inf")])
