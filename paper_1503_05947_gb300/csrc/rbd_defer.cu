@@ -36,6 +36,7 @@
 // kBarrierLimitNs); a wait that runs out raises RBD_ETIMEOUT and the abort bit of the barrier
 // word, and the CTAs leave at their next grid barrier after their copies in flight have landed.
 #include <algorithm>
+#include <climits>
 
 #include "rbd_device.cuh"
 #include "rbd_loop.cuh"
@@ -66,7 +67,7 @@ struct DeferParams {
     float* ysb;           // [G][2][d_max][RS] split Y, row-block-major
     float* vs;            // tile-interleaved split v1 (pivot-vector tiles of the pass)
     float* tf;            // [ngroups][d_max][C] T in FP32, group-blocked (the flush corrections)
-    double* hpart;        // [G][d_max]
+    double* hpart;        // [G][d_max] float-float pairs (hi, lo) of the partial second-sweep sums
     double* h;            // [d_max]
     double* nu2part;      // [G]
     double* pbest_e;      // [G]
@@ -101,7 +102,9 @@ __host__ __device__ inline DeferSmem defer_smem_layout(int R, int KC) {
     s.coef = o;
     o += (size_t)4 * KC * 4;                       // [h hi | h lo | t hi | t lo]
     s.tfb = o;
-    o += (size_t)KC * Cfg::C * 4;                  // T(0:k, group) in FP32
+    // T(0:k, group) in FP32 during the pass; the row-sum partials of F (4 NCONS doubles) before it
+    const size_t tfb_bytes = (size_t)KC * Cfg::C * 4, fp_bytes = (size_t)4 * NCONS * 8;
+    o += (tfb_bytes > fp_bytes) ? tfb_bytes : fp_bytes;
     s.corr = o;
     o += (size_t)Cfg::NW * Cfg::C * 4;             // flush corrections, per warp
     s.scratch = o;
@@ -203,7 +206,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
     const int ybuf = spb * STAGE;
     const int yplane = LC * RS;
     const float* ysrc = p.ysb + b * 2 * p.d_max * (int64_t)RS;
-    const uint64_t pol_y = l2_policy_evict_normal();
+    // Y slices and the FP32 T blocks are re-read every basis: kept in L2 against the X stream
+    const uint64_t pol_y = l2_policy_evict_last();
     const uint64_t pol_x = p.evict_first ? l2_policy_evict_first() : l2_policy_evict_normal();
     const uint64_t pol_v = l2_policy_evict_normal();
     const unsigned char* planes = p.planes;
@@ -214,8 +218,6 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
     int ps = 0;
     uint32_t pph = 0;
     bool preuse = false;
-    int64_t npref = 0;       // units whose X part is in the ring ahead of barrier 1
-    int pf_s0 = 0;
     uint32_t iss_par = 0, iss_mask = 0;  // parity and presence of the last issue into each stage
     // consumers (identical copies in every consumer thread)
     int cs = 0;
@@ -285,18 +287,23 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 split_f64_fast(t0, cbh[l], cbl[l]);
                 if (l + NCONS < ncol) split_f64_fast(t1, cbh[l + NCONS], cbl[l + NCONS]);
             }
+            // Generic-proxy writes (this CTA's columns of ysb) are read by bulk copies (the async
+            // proxy): the issuing thread orders them with a proxy fence after the barriers that made
+            // them visible to it (here and before every batch of copies below).
+            if (tid == 0 && ypre < min((int64_t)NB, ytot)) fence_proxy_async_global();
             for (int64_t u = ypre; u < min((int64_t)NB, ytot); ++u) y_issue(u, ncol, nch);
             ypre = 0;
             named_bar(1, NCONS);  // coefficients staged
 
-            const int NSUB = (R <= NCONS) ? (NCONS / R) : 1;
-            const int q = (R <= NCONS) ? (tid / R) : 0;
-            const int rfirst = (R <= NCONS) ? (tid % R) : tid;
-            const bool active = (R <= NCONS) ? (tid < NSUB * R) : true;
-            // B: float-float sums of Y t; A: Y h_{k-1}, plain FP32 when h is small, else float-float
-            float bs[MAXRPT], bc[MAXRPT], as[MAXRPT], ac[MAXRPT];
-#pragma unroll
-            for (int i = 0; i < MAXRPT; ++i) bs[i] = bc[i] = as[i] = ac[i] = 0.f;
+            // Row sums: thread (pair pr, segment sg) sums rows 2 pr and 2 pr + 1 over the columns sg,
+            // sg + NSG, ... of each chunk: four independent chains (two rows x B and A).  B = Y t in
+            // float-float; A = Y h_{k-1} in plain FP32 while h is small, else float-float.
+            const int NPR = R / 2;
+            const int NSG = max(1, NCONS / NPR);
+            const int pr = tid % NPR, sg = tid / NPR;
+            const bool active = sg < NSG;
+            const int rp = 2 * pr;
+            float b0s = 0.f, b0c = 0.f, b1s = 0.f, b1c = 0.f, a0s = 0.f, a0c = 0.f, a1s = 0.f, a1c = 0.f;
             const int amode = deferred ? (small_h ? 1 : 2) : 0;
             for (int64_t u = 0; u < nch; ++u) {
                 const int bf = (int)(u % NB);
@@ -309,26 +316,34 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 const float* cl = cbl + l0;
                 const float* hh = cah + l0;
                 const float* hl = cal + l0;
-                if (active && ok) {
-#pragma unroll
-                    for (int i = 0; i < MAXRPT; ++i) {
-                        const int r = rfirst + i * NCONS;
-                        if (r >= Rb || (R <= NCONS && i > 0)) break;
-                        if (amode == 1) {
-                            for (int l = q; l < lc; l += NSUB) {
-                                const float y0 = yh[l * RS + r], y1 = yl[l * RS + r];
-                                ff_mac2(bs[i], bc[i], y0, y1, ch[l], cl[l]);
-                                as[i] = __fmaf_rn(y0, hh[l], as[i]);
-                            }
-                        } else if (amode == 2) {
-                            for (int l = q; l < lc; l += NSUB) {
-                                const float y0 = yh[l * RS + r], y1 = yl[l * RS + r];
-                                ff_mac2(bs[i], bc[i], y0, y1, ch[l], cl[l]);
-                                ff_mac2(as[i], ac[i], y0, y1, hh[l], hl[l]);
-                            }
-                        } else {
-                            for (int l = q; l < lc; l += NSUB)
-                                ff_mac2(bs[i], bc[i], yh[l * RS + r], yl[l * RS + r], ch[l], cl[l]);
+                if (active && ok && rp < Rb) {
+                    if (amode == 1) {
+                        for (int l = sg; l < lc; l += NSG) {
+                            const float2 y = *reinterpret_cast<const float2*>(yh + l * RS + rp);
+                            const float2 z = *reinterpret_cast<const float2*>(yl + l * RS + rp);
+                            const float th = ch[l], tl = cl[l], ha = hh[l];
+                            ff_mac2(b0s, b0c, y.x, z.x, th, tl);
+                            ff_mac2(b1s, b1c, y.y, z.y, th, tl);
+                            a0s = __fmaf_rn(y.x, ha, a0s);
+                            a1s = __fmaf_rn(y.y, ha, a1s);
+                        }
+                    } else if (amode == 2) {
+                        for (int l = sg; l < lc; l += NSG) {
+                            const float2 y = *reinterpret_cast<const float2*>(yh + l * RS + rp);
+                            const float2 z = *reinterpret_cast<const float2*>(yl + l * RS + rp);
+                            const float th = ch[l], tl = cl[l], ha = hh[l], hb = hl[l];
+                            ff_mac2(b0s, b0c, y.x, z.x, th, tl);
+                            ff_mac2(b1s, b1c, y.y, z.y, th, tl);
+                            ff_mac2(a0s, a0c, y.x, z.x, ha, hb);
+                            ff_mac2(a1s, a1c, y.y, z.y, ha, hb);
+                        }
+                    } else {
+                        for (int l = sg; l < lc; l += NSG) {
+                            const float2 y = *reinterpret_cast<const float2*>(yh + l * RS + rp);
+                            const float2 z = *reinterpret_cast<const float2*>(yl + l * RS + rp);
+                            const float th = ch[l], tl = cl[l];
+                            ff_mac2(b0s, b0c, y.x, z.x, th, tl);
+                            ff_mac2(b1s, b1c, y.y, z.y, th, tl);
                         }
                     }
                 }
@@ -345,7 +360,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     const double xi = live ? (v1s[r] - A) * inv_prev : 0.0;
                     if (live) p.Y[(r0 + r) + (k - 1) * p.ldy] = xi;
                     float hi, lo;
-                    split_double(xi, hi, lo);
+                    split_f64_fast(xi, hi, lo);
                     p.ysb[(b * 2 + 0) * p.d_max * RS + (k - 1) * RS + r] = hi;
                     p.ysb[(b * 2 + 1) * p.d_max * RS + (k - 1) * RS + r] = lo;
                     xih[r] = hi;
@@ -354,34 +369,33 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 }
                 const double v = live ? (xr[i] - B) - xs * tlast : 0.0;
                 v1s[r] = v;
-                split_double(v, v1h[r], v1l[r]);
+                split_f64_fast(v, v1h[r], v1l[r]);
             };
-            if (R <= NCONS) {
-                if (active) {
-                    part[q * R + rfirst] = ff_to_double(bs[0], bc[0]);
-                    part[NCONS + q * R + rfirst] = (amode == 1) ? (double)as[0] : ff_to_double(as[0], ac[0]);
-                }
-                named_bar(1, NCONS);
-                if (tid < R) {
-                    double A = 0.0, B = 0.0;
-                    if (tid < Rb && ncol > 0)
-                        for (int qq = 0; qq < NSUB; ++qq) {
-                            B += part[qq * R + tid];
-                            A += part[NCONS + qq * R + tid];
-                        }
-                    fin(tid, 0, A, B);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < MAXRPT; ++i) {
-                    const int r = tid + i * NCONS;
-                    if (r >= R) break;
-                    const bool in = r < Rb && ncol > 0;
-                    fin(r, i, in ? ((amode == 1) ? (double)as[i] : ff_to_double(as[i], ac[i])) : 0.0,
-                        in ? ff_to_double(bs[i], bc[i]) : 0.0);
-                }
+            // the segments' partial sums of each row, added in FP64 in segment order (v1 = x - Y t
+            // cancels heavily when the pivot nearly lies in span(Y))
+            double* fpart = reinterpret_cast<double*>(tfb);  // [sg][pr][B0, B1, A0, A1]
+            if (active) {
+                double* o = fpart + ((size_t)sg * NPR + pr) * 4;
+                o[0] = ff_to_double(b0s, b0c);
+                o[1] = ff_to_double(b1s, b1c);
+                o[2] = (amode == 1) ? (double)a0s : ff_to_double(a0s, a0c);
+                o[3] = (amode == 1) ? (double)a1s : ff_to_double(a1s, a1c);
             }
-            fence_proxy_async_global();  // the new column of ysb is streamed by bulk copies later
+            named_bar(1, NCONS);
+#pragma unroll
+            for (int i = 0; i < MAXRPT; ++i) {
+                const int r = tid + i * NCONS;
+                if (r >= R) break;
+                double A = 0.0, B = 0.0;
+                if (r < Rb && ncol > 0) {
+                    const double* pin = fpart + (size_t)(r >> 1) * 4 + (r & 1);
+                    for (int sgi = 0; sgi < NSG; ++sgi) {
+                        B += pin[(size_t)sgi * NPR * 4];
+                        A += pin[(size_t)sgi * NPR * 4 + 2];
+                    }
+                }
+                fin(r, i, A, B);
+            }
             named_bar(1, NCONS);         // v1 and xi_{k-1} complete in shared memory
 
             // ---------------- O1': hpart[b] = Y_b(:, 0:k)' v1 ----------------
@@ -419,7 +433,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     float s0 = pf[2 * tid], c0 = pf[2 * tid + 1];
                     for (int sg = 1; sg < nseg; ++sg)
                         ff_add_acc(s0, c0, pf[2 * (sg * lc + tid)], pf[2 * (sg * lc + tid) + 1]);
-                    p.hpart[b * p.d_max + l0 + tid] = ff_to_double(s0, c0);
+                    // float-float; the service warp converts (FP64 off the critical path)
+                    reinterpret_cast<float2*>(p.hpart)[b * p.d_max + l0 + tid] = make_float2(s0, c0);
                 }
             };
             if (resident) {
@@ -441,10 +456,15 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             // ||v1||^2 of this block (fixed order) and the split v1 tiles of the pass: tile t holds
             // [hi(rows_t) | lo(rows_t)] at t * 2 * MT
             if (warp == 0) {
-                double acc = 0.0;
-                for (int r = lane; r < Rb; r += 32) acc += v1s[r] * v1s[r];
-                acc = warp_sum_double(acc);
-                if (lane == 0) p.nu2part[b] = acc;
+                // float-float squares of the split v1, a fixed lane tree (positive terms)
+                float s2 = 0.f, c2 = 0.f;
+                for (int r = lane; r < Rb; r += 32) ff_mac2(s2, c2, v1h[r], v1l[r], v1h[r], v1l[r]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float so = __shfl_xor_sync(0xffffffffu, s2, o), co = __shfl_xor_sync(0xffffffffu, c2, o);
+                    ff_add_acc(s2, c2, so, co);
+                }
+                if (lane == 0) p.nu2part[b] = ff_to_double(s2, c2);
             }
             for (int r = tid; r < Rb; r += NCONS) {
                 const int64_t row = r0 + r;
@@ -454,7 +474,6 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 p.vs[off] = v1h[r];
                 p.vs[off + rt] = v1l[r];
             }
-            fence_proxy_async_global();  // read by the pass's bulk copies
             named_bar_arrive(3, NCONS + 32);  // every consumer is done with the ring
         } else if (warp == PROD) {
             named_bar(2, NCONS + 32);
@@ -473,36 +492,6 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 }
             }
             named_bar(3, NCONS + 32);
-            if (lane == 0 && run_pass && ok) {
-                // ... and into the ring (their pivot-vector parts follow after barrier 1)
-                npref = min(nunits, (int64_t)S);
-                pf_s0 = ps;
-                int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
-                for (int64_t i = 0; i < npref; ++i) {
-                    if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
-                        loop_abort(ctl, p.bar, ST_ETIMEOUT);
-                        ok = false;
-                        npref = i;
-                        break;
-                    }
-                    const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
-                    const uint32_t x_bytes = (uint32_t)(C * UB) * rows;
-                    mbar_arrive_expect_tx(&full[ps], x_bytes);
-                    bulk_g2s(stages + (size_t)ps * STAGE + XI,
-                             planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE, x_bytes, &full[ps], pol_x);
-                    iss_mask |= 1u << ps;
-                    iss_par = (iss_par & ~(1u << ps)) | (pph << ps);
-                    if (++ps == S) {
-                        ps = 0;
-                        pph ^= 1u;
-                        preuse = true;
-                    }
-                    if (++t == NT) {
-                        t = 0;
-                        ++g;
-                    }
-                }
-            }
         }
         if (!grid_sync(p.bar, (uint32_t)G, gen, &sfl[0], ctl)) break;  // barrier 1 (uniform result)
 
@@ -510,6 +499,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
         if (warp == SVC) {
             // ---------------- second sweep over the grid: h, nu, the stop tests ----------------
             double nu2 = 0.0, fs = 0.0, hh = 0.0;
+            const double xn2p = (lane == 0) ? __ldg(&p.xn2[piv]) : 0.0;  // loads of this round first
 #pragma unroll 4
             for (int64_t bb = lane; bb < G; bb += 32) nu2 += __ldcg(&p.nu2part[bb]);
             if (k > 0) {
@@ -523,7 +513,10 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     for (int64_t bb = lane; bb < G; bb += 32)
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
-                            if (l + j < lb1) a4[j] += __ldcg(&p.hpart[bb * p.d_max + l + j]);
+                            if (l + j < lb1) {
+                                const float2 hv = __ldcg(reinterpret_cast<const float2*>(p.hpart) + bb * p.d_max + l + j);
+                                a4[j] += (double)hv.x + (double)hv.y;
+                            }
 #pragma unroll
                     for (int j = 0; j < 4; ++j) a4[j] = warp_sum_double(a4[j]);
                     if (lane == 0)
@@ -531,10 +524,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                             if (l + j < lb1) p.h[l + j] = a4[j];
                 }
                 __syncwarp();
-                if (lane == 0) {
-                    __threadfence();
-                    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p.hcnt) : "memory");
-                }
+                if (lane == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p.hcnt) : "memory");
                 ++hround;
                 if (!wait_counter(p.hcnt, p.bar, (uint32_t)G * hround)) {
                     if (lane == 0) loop_abort(ctl, p.bar, ST_ETIMEOUT);
@@ -542,10 +532,19 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 }
                 // h (every CTA, same order): ||h||^2, and its split for the corrections of this pass
                 // and the first stream of the next basis
-                for (int64_t l = lane; l < k; l += 32) {
-                    const double hv = ok ? __ldcg(&p.h[l]) : 0.0;
-                    hh += hv * hv;
-                    split_f64_fast(hv, cah[l], cal[l]);
+                for (int64_t l0 = 0; l0 < k; l0 += 32 * 16) {
+                    double hv[16];  // all loads in flight before the shared-memory stores
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t l = l0 + lane + 32 * j;
+                        hv[j] = (ok && l < k) ? __ldcg(&p.h[l]) : 0.0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t l = l0 + lane + 32 * j;
+                        hh += hv[j] * hv[j];
+                        if (l < k) split_f64_fast(hv[j], cah[l], cal[l]);
+                    }
                 }
                 hh = warp_sum_double(hh);
             }
@@ -554,7 +553,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             if (lane == 0) {
                 const double nuv = sqrt(fmax(nu2 - hh, 0.0));
                 const double frol = sqrt(fmax(fs, 0.0));
-                const double xin = sqrt(__ldg(&p.xn2[piv]));
+                const double xin = sqrt(xn2p);
                 int32_t st = STOP_NONE;
                 if (k > 0) {
                     if (mode == MODE_FRO_REL) {
@@ -590,20 +589,11 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
                 int64_t issued = nunits;
                 if (ok) {
-                    // pivot-vector tiles of the prefetched units, then the remaining units
-                    int sp = pf_s0;
-                    for (int64_t i = 0; i < npref; ++i) {
-                        const uint32_t rows = (uint32_t)min((int64_t)MT, p.ldp - t * MT);
-                        const uint32_t xi_bytes = 2u * rows * 4u;
-                        mbar_arrive_expect_tx(&full[sp], xi_bytes);
-                        bulk_g2s(stages + (size_t)sp * STAGE, p.vs + t * 2 * MT, xi_bytes, &full[sp], pol_v);
-                        if (++sp == S) sp = 0;
-                        if (++t == NT) {
-                            t = 0;
-                            ++g;
-                        }
-                    }
-                    for (int64_t i = npref; i < nunits; ++i) {
+                    fence_proxy_async_global();  // the v1 tiles every CTA wrote before barrier 1
+                    // Every unit, X part and pivot-vector part; the first units' X tiles were
+                    // prefetched into L2 during the orthogonalisation (issuing them into the ring
+                    // before barrier 1 would load the memory system the barrier's atomics cross).
+                    for (int64_t i = 0; i < nunits; ++i) {
                         if (mbar_try_wait(svcb, spar) && vfl[1] != STOP_NONE) {
                             issued = i;  // the basis was rejected: stop streaming
                             break;
@@ -636,9 +626,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                         }
                     }
                 } else {
-                    issued = npref;
+                    issued = 0;
                 }
-                npref = 0;
                 vfl[3] = (int)issued;
                 __threadfence_block();
                 vfl[4] = (int)(k + 1);
@@ -670,9 +659,10 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             if (run_pass) {
                 if (k > 0 && gtf0 <= glast) {
                     if (tid == 0) {
+                        fence_proxy_async_global();  // the T rows other CTAs wrote in earlier bases
                         const uint32_t bytes = (uint32_t)(k * C * 4);
                         mbar_arrive_expect_tx(tfull, bytes);
-                        bulk_g2s(tfb, p.tf + gtf0 * p.d_max * C, bytes, tfull, pol_v);
+                        bulk_g2s(tfb, p.tf + gtf0 * p.d_max * C, bytes, tfull, pol_y);
                     }
                     tf_pend = true;
                 }
@@ -681,11 +671,9 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 for (int qq = 0; qq < CPW; ++qq)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
-                double best_e = -1.0;
+                long long best_k = LLONG_MIN;  // running argmax of this lane's columns (lanes < CPW)
                 int64_t best_j = INT64_MAX;
-                double e_old[CPW];
-#pragma unroll
-                for (int qq = 0; qq < CPW; ++qq) e_old[qq] = 0.0;
+                double e_old = 0.0;            // e_j of this lane's column of the current group
                 int gbuf = 0;
                 bool cut = false;
                 double* gsum_k = p.gsum + (k & 1) * p.ngroups;
@@ -737,13 +725,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     }
                     const int64_t c0 = g * C;
                     const int ncols = (int)min((int64_t)C, p.n - c0);
-                    if (lane == 0 && (t == 0 || u == L0)) {
-#pragma unroll
-                        for (int qq = 0; qq < CPW; ++qq) {
-                            const int cw = warp * CPW + qq;
-                            if (cw < ncols) e_old[qq] = __ldcg(&p.e[c0 + cw]);
-                        }
-                    }
+                    if (lane < CPW && (t == 0 || u == L0) && warp * CPW + lane < ncols)
+                        e_old = __ldcg(&p.e[c0 + warp * CPW + lane]);
                     const int rows = (int)min((int64_t)MT, p.ldp - t * MT);
                     if (ok) {
                         const float* st = stages + (size_t)s * STAGE;
@@ -764,17 +747,31 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     if (t != NT - 1 && u != L1 - 1) continue;
 
                     // ---------------- end of this CTA's share of column group g ----------------
-                    double tot[CPW];
+                    // Each column's total over the warp (xor butterfly, a fixed order per lane); lane q
+                    // then finalises the warp's column q, so that the FP64 steps of the two columns run
+                    // side by side (dependent FP64 instructions are slow on this part).
+                    float ts = 0.f, tc = 0.f;
 #pragma unroll
                     for (int qq = 0; qq < CPW; ++qq) {
                         float sq = acc_s[qq][0], cq = acc_c[qq][0];
 #pragma unroll
                         for (int e = 1; e < 4; ++e) ff_add(sq, cq, acc_s[qq][e], acc_c[qq][e]);
-                        warp_sum_ff(sq, cq);
-                        tot[qq] = ff_to_double(sq, cq);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const float s2 = __shfl_xor_sync(0xffffffffu, sq, o);
+                            const float c2 = __shfl_xor_sync(0xffffffffu, cq, o);
+                            ff_add(sq, cq, s2, c2);
+                        }
+                        if (lane == qq) {
+                            ts = sq;
+                            tc = cq;
+                        }
 #pragma unroll
                         for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
                     }
+                    const int cwl = warp * CPW + lane;  // this lane's column of the group (lanes < CPW)
+                    const bool colv = lane < CPW && cwl < ncols;
+                    double tot = colv ? ff_to_double(ts, tc) : 0.0;
                     const bool tf_here = k > 0 && g >= gtf0;  // this group's T block was streamed
                     if (tf_here) {
                         if (ok && !mbar_wait(tfull, tcnt & 1u)) {
@@ -793,12 +790,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                         const int64_t blast = unit_owner(g * NT + NT - 1, W, G);
                         const uint32_t ncontrib = (uint32_t)(blast - bfirst + 1);
                         const int64_t slot = b - bfirst;
-                        if (lane == 0) {
-#pragma unroll
-                            for (int qq = 0; qq < CPW; ++qq) {
-                                const int cw = warp * CPW + qq;
-                                if (cw < ncols) p.gslot[(g * p.KMAX + slot) * C + cw] = tot[qq];
-                            }
+                        if (colv) {
+                            p.gslot[(g * p.KMAX + slot) * C + cwl] = tot;
                             __threadfence();
                         }
                         named_bar(1, NCONS);
@@ -807,17 +800,11 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                         fin_here = vfl[2] != 0;
                         if (fin_here) {
                             __threadfence();
-                            if (lane == 0) {
-#pragma unroll
-                                for (int qq = 0; qq < CPW; ++qq) {
-                                    const int cw = warp * CPW + qq;
-                                    if (cw < ncols) {
-                                        double acc = 0.0;
-                                        for (uint32_t sl = 0; sl < ncontrib; ++sl)
-                                            acc += __ldcg(&p.gslot[(g * p.KMAX + sl) * C + cw]);
-                                        tot[qq] = acc;
-                                    }
-                                }
+                            if (colv) {
+                                double acc = 0.0;
+                                for (uint32_t sl = 0; sl < ncontrib; ++sl)
+                                    acc += __ldcg(&p.gslot[(g * p.KMAX + sl) * C + cwl]);
+                                tot = acc;
                             }
                             if (tid == 0) p.gcnt[g] = 0;
                         }
@@ -852,12 +839,13 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                                 const float c2 = __shfl_xor_sync(0xffffffffu, cc, o);
                                 ff_add(s, cc, s2, c2);
                             }
-                            const double cr = ff_to_double(s, cc);
-                            const double cr1 = __shfl_sync(0xffffffffu, cr, 16);
-                            if (lane == 0) {
-                                tot[0] -= cr;
-                                tot[1] -= cr1;
+                            // lane 0 holds column 0's sum, lane 16 column 1's: to lanes 0 and 1
+                            const float s1 = __shfl_sync(0xffffffffu, s, 16), c1 = __shfl_sync(0xffffffffu, cc, 16);
+                            if (lane == 1) {
+                                s = s1;
+                                cc = c1;
                             }
+                            if (colv) tot -= ff_to_double(s, cc);
                         } else if (k > 0) {
                             // FP32: the term is ||h|| / nu <= 2^-29 relative to the column's norm
                             const int c = tid % C, ls = tid / C;
@@ -871,45 +859,34 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                             sacc = __fadd_rn(sacc, __shfl_xor_sync(0xffffffffu, sacc, 16));
                             if (lane < 16) corr[warp * C + lane] = sacc;
                             named_bar(1, NCONS);
-                            if (lane == 0) {
+                            if (colv) {
+                                float cr = 0.f;
 #pragma unroll
-                                for (int qq = 0; qq < CPW; ++qq) {
-                                    const int cw = warp * CPW + qq;
-                                    float cr = 0.f;
-#pragma unroll
-                                    for (int w = 0; w < NW; ++w) cr = __fadd_rn(cr, corr[w * C + cw]);
-                                    tot[qq] -= (double)cr;
-                                }
+                                for (int w = 0; w < NW; ++w) cr = __fadd_rn(cr, corr[w * C + cwl]);
+                                tot -= (double)cr;
                             }
                         }
-                        if (lane == 0) {
-#pragma unroll
-                            for (int qq = 0; qq < CPW; ++qq) {
-                                const int cw = warp * CPW + qq;
-                                if (cw < ncols) {
-                                    const int64_t j = c0 + cw;
-                                    const double cj = tot[qq] * inv_nu;
-                                    p.T[j * p.ldt + k] = cj;
-                                    p.tf[(g * p.d_max + k) * C + cw] = __double2float_rn(cj);
-                                    const double en = (j == piv) ? 0.0 : fmax(e_old[qq] - cj * cj, 0.0);
-                                    p.e[j] = en;
-                                    grp_e[gbuf * C + cw] = en;
-                                    if (better(en, j, best_e, best_j)) {
-                                        best_e = en;
-                                        best_j = j;
-                                    }
-                                }
+                        if (colv) {
+                            const int64_t j = c0 + cwl;
+                            const double cj = tot * inv_nu;
+                            p.T[j * p.ldt + k] = cj;
+                            p.tf[(g * p.d_max + k) * C + cwl] = __double2float_rn(cj);
+                            const double en = (j == piv) ? 0.0 : fmax(e_old - cj * cj, 0.0);
+                            p.e[j] = en;
+                            grp_e[gbuf * C + cwl] = en;
+                            const long long ek = __double_as_longlong(en);  // e >= 0: ordered as integers
+                            if (better_key(ek, j, best_k, best_j)) {
+                                best_k = ek;
+                                best_j = j;
                             }
-                            fence_proxy_async_global();  // this row of the FP32 T is streamed later
                         }
-                        // one barrier per group: thread 0 sums this buffer while the other warps move
-                        // on; it is written again two groups later, after thread 0 passed the next
-                        // barrier
                         named_bar(1, NCONS);
-                        if (tid == 0) {
-                            double sacc = 0.0;
-                            for (int cw = 0; cw < ncols; ++cw) sacc += grp_e[gbuf * C + cw];
-                            gsum_k[g] = sacc;
+                        // the group's sum of e_j: warp 0, a fixed tree over the group's columns
+                        if (warp == 0) {
+                            double sv = (lane < ncols && lane < C) ? grp_e[gbuf * C + lane] : 0.0;
+#pragma unroll
+                            for (int o = C / 2; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+                            if (lane == 0) gsum_k[g] = sv;
                         }
                         gbuf ^= 1;
                     }
@@ -919,27 +896,38 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                             const uint32_t bytes = (uint32_t)(k * C * 4);
                             mbar_arrive_expect_tx(tfull, bytes);
-                            bulk_g2s(tfb, p.tf + (g + 1) * p.d_max * C, bytes, tfull, pol_v);
+                            bulk_g2s(tfb, p.tf + (g + 1) * p.d_max * C, bytes, tfull, pol_y);
                         }
                         tf_pend = true;
                     }
                 }
                 get_dec();  // a CTA that finalised no group learns the decision here
                 if (dec == STOP_NONE) {
+#pragma unroll
+                    for (int o = 1; o < CPW; o <<= 1) {
+                        const long long ok2 = __shfl_xor_sync(0xffffffffu, best_k, o);
+                        const int64_t oj2 = __shfl_xor_sync(0xffffffffu, best_j, o);
+                        if (better_key(ok2, oj2, best_k, best_j)) {
+                            best_k = ok2;
+                            best_j = oj2;
+                        }
+                    }
                     if (lane == 0) {
-                        red_e[warp] = best_e;
+                        red_e[warp] = __longlong_as_double(best_k);
                         red_j[warp] = best_j;
                     }
                     named_bar(1, NCONS);
                     if (tid == 0) {
-                        double be = -1.0;
+                        long long bk = LLONG_MIN;
                         int64_t bj = INT64_MAX;
-                        for (int w = 0; w < NW; ++w)
-                            if (better(red_e[w], red_j[w], be, bj)) {
-                                be = red_e[w];
+                        for (int w = 0; w < NW; ++w) {
+                            const long long wk = __double_as_longlong(red_e[w]);
+                            if (better_key(wk, red_j[w], bk, bj)) {
+                                bk = wk;
                                 bj = red_j[w];
                             }
-                        p.pbest_e[b] = be;
+                        }
+                        p.pbest_e[b] = __longlong_as_double(bk);  // the key's bits (e_j itself, or none)
                         p.pbest_j[b] = bj;
                     }
                 }
@@ -952,6 +940,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 const int64_t ncol2 = k, nch2 = ceil_div(ncol2, (int64_t)LC);
                 const int64_t tot2 = (nch2 <= NB) ? nch2 : 2 * nch2;
                 ypre = min((int64_t)NB, tot2);
+                if (tid == 0 && ypre > 0) fence_proxy_async_global();
                 for (int64_t u = 0; u < ypre; ++u) y_issue(u, ncol2, nch2);
             }
         }
@@ -967,23 +956,24 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
 
         // ---------------- A: argmax over CTAs ----------------
         if (warp == 0) {
-            double be = -1.0;
+            // keys compared as integers: e_j >= 0, whose FP64 bit patterns order like the values
+            long long bk = LLONG_MIN;
             int64_t bj = INT64_MAX;
 #pragma unroll 8
             for (int64_t cb = lane; cb < G; cb += 32) {
-                const double ce = __ldcg(&p.pbest_e[cb]);
+                const long long ck = __ldcg(reinterpret_cast<const long long*>(&p.pbest_e[cb]));
                 const int64_t cj = __ldcg(reinterpret_cast<const long long*>(&p.pbest_j[cb]));
-                if (better(ce, cj, be, bj)) {
-                    be = ce;
+                if (better_key(ck, cj, bk, bj)) {
+                    bk = ck;
                     bj = cj;
                 }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double oe = __shfl_down_sync(0xffffffffu, be, o);
+                const long long ok2 = __shfl_down_sync(0xffffffffu, bk, o);
                 const int64_t oj = __shfl_down_sync(0xffffffffu, bj, o);
-                if (better(oe, oj, be, bj)) {
-                    be = oe;
+                if (better_key(ok2, oj, bk, bj)) {
+                    bk = ok2;
                     bj = oj;
                 }
             }
@@ -1005,8 +995,6 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
 
     // ---------------- leave: no bulk copy may still be writing this CTA's shared memory ----------------
     if (warp == PROD && lane == 0) {
-        // X parts prefetched ahead of a barrier that failed: complete those phases' second arrival
-        for (int64_t i = 0; i < npref; ++i) mbar_arrive(&full[(pf_s0 + (int)i) % S]);
         for (int s = 0; s < S; ++s)
             if ((iss_mask >> s) & 1u)
                 if (!mbar_wait(&full[s], (iss_par >> s) & 1u)) {

@@ -202,6 +202,12 @@ __device__ __forceinline__ double recip_pos(double x) {
     return y;
 }
 
+// The same order on integer keys: the FP64 bit patterns of non-negative values (which order like
+// the values), LLONG_MIN for no candidate; integer compares avoid the slow FP64 pipe.
+__device__ __forceinline__ bool better_key(long long k1, int64_t j1, long long k0, int64_t j0) {
+    return (k1 > k0) || (k1 == k0 && j1 < j0);
+}
+
 // (value, index) max with ties to the lowest index; invalid entries carry index INT64_MAX.
 __device__ __forceinline__ bool better(double e1, int64_t j1, double e0, int64_t j0) {
     return (e1 > e0) || (e1 == e0 && j1 < j0);
@@ -263,6 +269,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ uint64_t l2_policy_evict_first() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 

@@ -57,9 +57,10 @@ __device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint3
     if (threadIdx.x == 0) {
         int ok = 1;
         const uint32_t target = nblocks * (++gen);
-        uint32_t v;
-        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(bar) : "memory");
-        v += 1;
+        // arrival without a returned value (no round trip before the first poll); the first poll
+        // of the same word already sees it
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        uint32_t v = ld_acquire_u32(bar);
         if (!(v & kAbortBit) && v < target) {
             const uint64_t t0 = globaltimer_ns();
             while (true) {

@@ -59,10 +59,16 @@ __global__ void __launch_bounds__(256) resume_state_kernel(ResumeParams p) {
             }
             p.e[j] = e;
         }
-        // the group's sum of e_j, columns in order
+        // the group's sum of e_j in the order of the path that continues: columns in order, or
+        // (two-barrier loop kernel) the fixed tree over the group's 16 lanes
         const int ncols = (int)min((int64_t)p.C, p.n - g * p.C);
         double s = 0.0;
-        for (int cw = 0; cw < ncols; ++cw) s += __shfl_sync(0xffffffffu, e, cw);
+        if (p.tf) {
+            s = (lane < ncols) ? e : 0.0;
+            for (int o = p.C / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        } else {
+            for (int cw = 0; cw < ncols; ++cw) s += __shfl_sync(0xffffffffu, e, cw);
+        }
         if (lane == 0) p.gsum[g] = s;
     }
 }
