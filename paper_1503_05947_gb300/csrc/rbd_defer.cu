@@ -69,7 +69,7 @@ struct DeferParams {
     float* tf;            // [ngroups][d_max][C] T in FP32, group-blocked (the flush corrections)
     double* hpart;        // [G][d_max] float-float pairs (hi, lo) of the partial second-sweep sums
     double* h;            // [d_max]
-    double* nu2part;      // [G]
+    double* nu2part;      // [G] float-float pairs: each block's ||v1||^2
     double* pbest_e;      // [G]
     int64_t* pbest_j;     // [G]
     uint32_t* gcnt;
@@ -401,15 +401,20 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             // ---------------- O1': hpart[b] = Y_b(:, 0:k)' v1 ----------------
             // One thread per (column, row segment) of a chunk, four float-float chains over quads
             // of rows, the segments combined in order through shared memory.
-            auto dots_chunk = [&](const float* yh, const float* yl, int64_t l0, int lc) {
-                const int nseg = max(1, min(8, NCONS / lc));
+            // Columns lc, lc + 1 of the last call (nx = 2, or 1 without a deferred column) are the new
+            // column xi_{k-1} and v1 itself, both from shared memory: its hpart entry and this block's
+            // ||v1||^2 come out of the same pass over the chunk's rows.
+            auto dots_chunk = [&](const float* yh, const float* yl, int64_t l0, int lc, int nx) {
+                const int lt = lc + nx;
+                const int nseg = max(1, min(8, NCONS / lt));
                 const int sq = (NQ + nseg - 1) / nseg;
                 float* pf = reinterpret_cast<float*>(part) + ((dcount++ & 1u) ? 2 * NCONS : 0);
-                if (tid < nseg * lc) {
-                    const int l = tid % lc, sg = tid / lc;
+                if (tid < nseg * lt) {
+                    const int l = tid % lt, sg = tid / lt;
                     const int q0 = sg * sq, q1 = min(NQ, q0 + sq);
-                    const float* ch = yh + l * RS;
-                    const float* cl = yl + l * RS;
+                    const bool vcol = l >= lc && (l > lc || !deferred);  // the v1 column
+                    const float* ch = (l < lc) ? yh + l * RS : vcol ? v1h : xih;
+                    const float* cl = (l < lc) ? yl + l * RS : vcol ? v1l : xil;
                     float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
                     if (ok)
                         for (int qq = q0; qq < q1; ++qq) {
@@ -425,22 +430,31 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     ff_add_acc(s4[0], c4[0], s4[1], c4[1]);
                     ff_add_acc(s4[2], c4[2], s4[3], c4[3]);
                     ff_add_acc(s4[0], c4[0], s4[2], c4[2]);
-                    pf[2 * (sg * lc + l)] = s4[0];
-                    pf[2 * (sg * lc + l) + 1] = c4[0];
+                    pf[2 * (sg * lt + l)] = s4[0];
+                    pf[2 * (sg * lt + l) + 1] = c4[0];
                 }
                 named_bar(1, NCONS);
-                if (tid < lc) {
+                if (tid < lt) {
                     float s0 = pf[2 * tid], c0 = pf[2 * tid + 1];
                     for (int sg = 1; sg < nseg; ++sg)
-                        ff_add_acc(s0, c0, pf[2 * (sg * lc + tid)], pf[2 * (sg * lc + tid) + 1]);
+                        ff_add_acc(s0, c0, pf[2 * (sg * lt + tid)], pf[2 * (sg * lt + tid) + 1]);
                     // float-float; the service warp converts (FP64 off the critical path)
-                    reinterpret_cast<float2*>(p.hpart)[b * p.d_max + l0 + tid] = make_float2(s0, c0);
+                    const float2 r2 = make_float2(s0, c0);
+                    if (tid < lc)
+                        reinterpret_cast<float2*>(p.hpart)[b * p.d_max + l0 + tid] = r2;
+                    else if (tid > lc || !deferred)
+                        reinterpret_cast<float2*>(p.nu2part)[b] = r2;
+                    else
+                        reinterpret_cast<float2*>(p.hpart)[b * p.d_max + k - 1] = r2;
                 }
             };
-            if (resident) {
+            const int nx = deferred ? 2 : 1;
+            if (nch == 0) {
+                dots_chunk(nullptr, nullptr, 0, 0, nx);
+            } else if (resident) {
                 for (int64_t u = 0; u < nch; ++u) {
                     const float* yh = stages + (size_t)(u % NB) * ybuf;
-                    dots_chunk(yh, yh + yplane, u * LC, (int)min((int64_t)LC, ncol - u * LC));
+                    dots_chunk(yh, yh + yplane, u * LC, (int)min((int64_t)LC, ncol - u * LC), (u == nch - 1) ? nx : 0);
                 }
             } else {
                 for (int64_t u = nch; u < 2 * nch; ++u) {
@@ -448,24 +462,11 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     y_wait(bf);
                     const float* yh = stages + (size_t)bf * ybuf;
                     const int64_t l0 = (u - nch) * LC;
-                    dots_chunk(yh, yh + yplane, l0, (int)min((int64_t)LC, ncol - l0));
+                    dots_chunk(yh, yh + yplane, l0, (int)min((int64_t)LC, ncol - l0), (u == 2 * nch - 1) ? nx : 0);
                     if (u + NB < ytot) y_issue(u + NB, ncol, nch);  // dots_chunk's barrier freed it
                 }
             }
-            if (deferred) dots_chunk(xih, xil, k - 1, 1);
-            // ||v1||^2 of this block (fixed order) and the split v1 tiles of the pass: tile t holds
-            // [hi(rows_t) | lo(rows_t)] at t * 2 * MT
-            if (warp == 0) {
-                // float-float squares of the split v1, a fixed lane tree (positive terms)
-                float s2 = 0.f, c2 = 0.f;
-                for (int r = lane; r < Rb; r += 32) ff_mac2(s2, c2, v1h[r], v1l[r], v1h[r], v1l[r]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float so = __shfl_xor_sync(0xffffffffu, s2, o), co = __shfl_xor_sync(0xffffffffu, c2, o);
-                    ff_add_acc(s2, c2, so, co);
-                }
-                if (lane == 0) p.nu2part[b] = ff_to_double(s2, c2);
-            }
+            // the split v1 tiles of the pass: tile t holds [hi(rows_t) | lo(rows_t)] at t * 2 * MT
             for (int r = tid; r < Rb; r += NCONS) {
                 const int64_t row = r0 + r;
                 const int64_t t = row / MT;
@@ -501,7 +502,10 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             double nu2 = 0.0, fs = 0.0, hh = 0.0;
             const double xn2p = (lane == 0) ? __ldg(&p.xn2[piv]) : 0.0;  // loads of this round first
 #pragma unroll 4
-            for (int64_t bb = lane; bb < G; bb += 32) nu2 += __ldcg(&p.nu2part[bb]);
+            for (int64_t bb = lane; bb < G; bb += 32) {
+                const float2 nv = __ldcg(reinterpret_cast<const float2*>(p.nu2part) + bb);
+                nu2 += (double)nv.x + (double)nv.y;
+            }
             if (k > 0) {
                 const double* gs = p.gsum + ((k - 1) & 1) * p.ngroups;
 #pragma unroll 8
@@ -1022,11 +1026,12 @@ size_t defer_smem_bytes(int xt, int R, int KC) {
     return 0;
 }
 
+// Y columns per streamed chunk; at most 252 so that the last chunk's two extra columns (the new
+// basis vector and v1) still give every column a thread in the column dots.
 int defer_chunk_cols(int xt, int RS) {
-    if (xt == 0) return loop_chunk_cols<TileCfg<0>>(RS);
-    if (xt == 1) return loop_chunk_cols<TileCfg<1>>(RS);
-    if (xt == 2) return loop_chunk_cols<TileCfg<2>>(RS);
-    return 0;
+    const int lc = (xt == 0) ? loop_chunk_cols<TileCfg<0>>(RS) : (xt == 1) ? loop_chunk_cols<TileCfg<1>>(RS)
+                 : (xt == 2) ? loop_chunk_cols<TileCfg<2>>(RS) : 0;
+    return lc < 252 ? lc : 252;
 }
 
 static const void* defer_fn(int xt) {
