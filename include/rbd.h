@@ -413,6 +413,18 @@ typedef struct rbd_profile {
 } rbd_profile;
 
 void rbd_set_profiling(int enabled);
+
+/*
+ * rbd_set_wait_limit -- bound, in nanoseconds, on every device-side wait of the persistent kernels
+ * launched from now on (the loop kernels of rbd_compress and its variants, and the batched run):
+ * grid barriers, shared-memory barrier phases, team barriers.  A wait that runs out does not
+ * trap: the kernel records RBD_ETIMEOUT, its CTAs leave at their next barrier once their copies
+ * in flight have landed, and the call returns RBD_ETIMEOUT (a batched run marks the matrices it
+ * stopped).  0 restores the defaults (2 s for barrier waits, 10 s for a batched team barrier).
+ * Process-wide; returns the previous setting.  The paper has no counterpart: this is the
+ * failure-detection bound of the GPU path, settable so that tests can make a wait run out.
+ */
+uint64_t rbd_set_wait_limit(uint64_t ns);
 rbd_status rbd_get_profile(rbd_profile* out);
 
 const char* rbd_status_string(rbd_status s);

@@ -20,6 +20,7 @@ from .rbd import (  # noqa: F401
     project,
     reconstruct,
     set_profiling,
+    set_wait_limit,
     status_string,
     version,
     workspace_bytes,

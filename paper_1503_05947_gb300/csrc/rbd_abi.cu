@@ -295,6 +295,12 @@ static void progress_release(int slot) {
 // Profiling (CUDA events around launches, per host thread)
 // ---------------------------------------------------------------------------------------
 static std::atomic<int> g_profiling{0};
+static std::atomic<uint64_t> g_wait_ns{0};
+
+uint64_t wait_limit_ns(uint64_t dflt) {
+    const uint64_t v = g_wait_ns.load();
+    return v ? v : dflt;
+}
 static thread_local rbd_profile t_profile = {};
 
 rbd_status map_cuda(cudaError_t e) {
@@ -688,6 +694,8 @@ rbd_status rbd_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy, c
 }
 
 void rbd_set_profiling(int enabled) { g_profiling.store(enabled ? 1 : 0); }
+
+uint64_t rbd_set_wait_limit(uint64_t ns) { return g_wait_ns.exchange(ns); }
 
 rbd_status rbd_get_profile(rbd_profile* out) {
     if (!out) return RBD_EINVAL;

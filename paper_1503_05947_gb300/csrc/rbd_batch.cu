@@ -97,6 +97,8 @@ struct BatchParams {
     int32_t* status;             // per matrix (zero before the run)
     rbd_batch_result* res;
     int S;                       // ring stages used by the pass (<= SMAX)
+    uint64_t wait_ns;            // bound on a ring or Y-chunk wait (the exit drain keeps kWaitLimitNs)
+    uint64_t team_ns;            // bound on a team barrier
 };
 
 constexpr uint64_t kTeamWaitNs = 10000000000ull;  // a member may wait for teams ahead to finish
@@ -220,6 +222,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
 
     bool ok = true;
     uint32_t ycount = 0;          // Y chunks streamed so far (buffer and parity of each)
+    uint32_t yiss = 0, ywait = 0; // thread 0: chunks issued / waited (those in between are landing)
+    uint32_t iss_par = 0, iss_mask = 0;  // producer: parity and presence of the last issue per stage
     int ps = 0, cs = 0;           // pass ring: producer / consumer stage and phase
     uint32_t pph = 0, cph = 0;
     bool preuse = false;
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 if (ld_acquire_u32b(I.bar) < target) {
                     const uint64_t t0 = globaltimer_ns();
                     while (ld_acquire_u32b(I.bar) < target) {
-                        if (globaltimer_ns() - t0 > kTeamWaitNs) {
+                        if (globaltimer_ns() - t0 > bp.team_ns) {
                             good = 0;
                             break;
                         }
@@ -315,6 +319,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 const int64_t l0 = c * LC;
                 const int lc = (int)min((int64_t)LC, k - l0);
                 const uint32_t bytes = (uint32_t)(lc * rb * 4);
+                yiss = max(yiss, ycount + (uint32_t)c + 1u);
                 mbar_arrive_expect_tx(&ybar[bf], 2u * bytes);
                 bulk_g2s(ring + bf * buf_f, ysb + l0 * rb, bytes, &ybar[bf], pol_y);
                 bulk_g2s(ring + bf * buf_f + (int64_t)LC * rb, ysb + (dmax + l0) * rb, bytes, &ybar[bf], pol_y);
@@ -329,7 +334,10 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 const int64_t l0 = c * LC;
                 const int lc = (int)min((int64_t)LC, k - l0);
                 const uint32_t par = ((ycount + (uint32_t)c) / (uint32_t)kBNB) & 1u;
-                if (ok && !mbar_wait(&ybar[bf], par)) ok = false;
+                if (ok) {
+                    if (mbar_wait(&ybar[bf], par, bp.wait_ns)) ywait = max(ywait, ycount + (uint32_t)c + 1u);
+                    else ok = false;
+                }
                 if (ok) body(ring + bf * buf_f, ring + bf * buf_f + (int64_t)LC * rb, cst_h + l0, cst_l + l0, l0, lc);
                 named_bar(1, kBNCONS);  // chunk c consumed: its buffer may be refilled
                 post(l0, lc);
@@ -524,7 +532,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 if (lane == 0 && ok) {
                     int64_t g = g_lo, t = 0;
                     for (int64_t u = 0; u < W; ++u) {
-                        if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                        if (preuse && !mbar_wait(&empty[ps], pph ^ 1u, bp.wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -533,6 +541,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                         mbar_arrive_expect_tx(&full[ps], bytes);
                         bulk_g2s(ring + (size_t)ps * STAGE_F, I.planes + g * kBC * P * ldp + t * kBC * P * kBMT, bytes,
                                  &full[ps], pol_x);
+                        iss_mask |= 1u << ps;
+                        iss_par = (iss_par & ~(1u << ps)) | (pph << ps);
                         if (++ps == S) {
                             ps = 0;
                             pph ^= 1u;
@@ -569,7 +579,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                         const int cw = warp * kBCPW + lane;
                         e_old = (cw < ncols) ? __ldcg(&I.e[c0 + cw]) : 0.0;
                     }
-                    if (ok && !mbar_wait(&full[s], ph)) ok = false;
+                    if (ok && !mbar_wait(&full[s], ph, bp.wait_ns)) ok = false;
                     const int rows = (int)min((int64_t)kBMT, ldp - t * kBMT);
                     if (ok) {
                         const float* st = ring + (size_t)s * STAGE_F;
@@ -700,6 +710,13 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
         __syncthreads();
         if (!ok) break;
     }
+    // No bulk copy may still be writing this CTA's shared memory when it exits (a wait that gave
+    // up leaves copies in flight): these waits keep the default bound.
+    if (warp == kBNW && lane == 0)
+        for (int s = 0; s < SMAX; ++s)
+            if ((iss_mask >> s) & 1u) mbar_wait(&full[s], (iss_par >> s) & 1u);
+    if (tid == 0)
+        for (uint32_t gc = ywait; gc < yiss; ++gc) mbar_wait(&ybar[gc % (uint32_t)kBNB], (gc / (uint32_t)kBNB) & 1u);
 }
 
 template <int P>
@@ -875,6 +892,8 @@ rbd_status run_with(rbd_batch_plan p, rbd_batch_result* results, cudaStream_t st
     bp.status = p->d_status;
     bp.res = results;
     bp.S = S;
+    bp.wait_ns = wait_limit_ns(kWaitLimitNs);
+    bp.team_ns = wait_limit_ns(kTeamWaitNs);
     cudaError_t e = cudaMemsetAsync(p->d_queue, 0, p->zero_bytes, st);
     if (e != cudaSuccess) return cuda_status(e);
     void* args[] = {&bp};

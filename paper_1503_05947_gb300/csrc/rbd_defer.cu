@@ -76,6 +76,7 @@ struct DeferParams {
     double* gslot;
     double* gsum;         // [2][ngroups]: per-group sums of e_j, by parity of the basis
     int R, RS, LC, KC;
+    uint64_t wait_ns;     // bound on every wait of the loop (the exit drains keep kWaitLimitNs)
 };
 
 struct DeferSmem {
@@ -115,14 +116,15 @@ __host__ __device__ inline DeferSmem defer_smem_layout(int R, int KC) {
 
 // Spin on the h counter until it reaches target (all lanes of the warp read the same word);
 // false if the abort bit appeared or kBarrierLimitNs elapsed.
-__device__ __forceinline__ bool wait_counter(const uint32_t* cnt, const uint32_t* bar, uint32_t target) {
+__device__ __forceinline__ bool wait_counter(const uint32_t* cnt, const uint32_t* bar, uint32_t target,
+                                             uint64_t limit_ns) {
     if (ld_acquire_u32(cnt) >= target) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 0;; ++it) {
         if (ld_acquire_u32(cnt) >= target) return true;
         if ((it & 63u) == 63u) {
             if (*(volatile const uint32_t*)bar & kAbortBit) return false;
-            if (globaltimer_ns() - t0 > kBarrierLimitNs) return false;
+            if (globaltimer_ns() - t0 > limit_ns) return false;
         }
     }
 }
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             ypend |= 1u << bf;
         };
         auto y_wait = [&](int bf) {
-            if (ok && !mbar_wait(&ybar[bf], (ypar >> bf) & 1u)) {
+            if (ok && !mbar_wait(&ybar[bf], (ypar >> bf) & 1u, p.wait_ns)) {
                 loop_abort(ctl, p.bar, ST_ETIMEOUT);
                 ok = false;
             }
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             }
             named_bar(3, NCONS + 32);
         }
-        if (!grid_sync(p.bar, (uint32_t)G, gen, &sfl[0], ctl)) break;  // barrier 1 (uniform result)
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sfl[0], ctl, p.wait_ns)) break;  // barrier 1 (uniform result)
 
         int32_t dec = STOP_NONE;
         if (warp == SVC) {
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 __syncwarp();
                 if (lane == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p.hcnt) : "memory");
                 ++hround;
-                if (!wait_counter(p.hcnt, p.bar, (uint32_t)G * hround)) {
+                if (!wait_counter(p.hcnt, p.bar, (uint32_t)G * hround, p.wait_ns)) {
                     if (lane == 0) loop_abort(ctl, p.bar, ST_ETIMEOUT);
                     ok = false;
                 }
@@ -602,7 +604,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                             issued = i;  // the basis was rejected: stop streaming
                             break;
                         }
-                        if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                        if (preuse && !mbar_wait(&empty[ps], pph ^ 1u, p.wait_ns)) {
                             loop_abort(ctl, p.bar, ST_ETIMEOUT);
                             ok = false;
                             issued = i;
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 vfl[4] = (int)(k + 1);
             }
             __syncwarp();
-            if (ok && !mbar_wait(svcb, spar)) {
+            if (ok && !mbar_wait(svcb, spar, p.wait_ns)) {
                 if (lane == 0) loop_abort(ctl, p.bar, ST_ETIMEOUT);
                 ok = false;
             }
@@ -649,7 +651,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 if (have_dec) return;
                 if (tid == 0) {
                     int d = STOP_NONE;
-                    if (ok && !mbar_wait(svcb, spar)) {
+                    if (ok && !mbar_wait(svcb, spar, p.wait_ns)) {
                         loop_abort(ctl, p.bar, ST_ETIMEOUT);
                     } else {
                         d = vfl[1];
@@ -707,7 +709,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                                 got = false;
                                 break;
                             }
-                            if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                            if (globaltimer_ns() - t0 > p.wait_ns) {
                                 loop_abort(ctl, p.bar, ST_ETIMEOUT);
                                 ok = false;
                                 break;
@@ -778,7 +780,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     double tot = colv ? ff_to_double(ts, tc) : 0.0;
                     const bool tf_here = k > 0 && g >= gtf0;  // this group's T block was streamed
                     if (tf_here) {
-                        if (ok && !mbar_wait(tfull, tcnt & 1u)) {
+                        if (ok && !mbar_wait(tfull, tcnt & 1u, p.wait_ns)) {
                             loop_abort(ctl, p.bar, ST_ETIMEOUT);
                             ok = false;
                         }
@@ -956,7 +958,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             stop = dec;
             break;
         }
-        if (!grid_sync(p.bar, (uint32_t)G, gen, &sfl[0], ctl)) break;  // barrier 2 (uniform result)
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sfl[0], ctl, p.wait_ns)) break;  // barrier 2 (uniform result)
 
         // ---------------- A: argmax over CTAs ----------------
         if (warp == 0) {
@@ -1092,6 +1094,7 @@ cudaError_t launch_defer(const Work& w, const void* X, double* Y, int64_t ldy, d
     p.RS = w.RS;
     p.LC = w.LC;
     p.KC = w.KC;
+    p.wait_ns = wait_limit_ns(kWaitLimitNs);
     void* args[] = {&p};
     const int threads =
         32 + ((w.xt == 0) ? TileCfg<0>::THREADS : (w.xt == 1) ? TileCfg<1>::THREADS : TileCfg<2>::THREADS);

@@ -82,6 +82,7 @@ struct LoopParams {
     double* gslot;
     double* gslot2;       // A-norm form: group partials of the dot products with z
     double* gsum;
+    uint64_t wait_ns;     // bound on every wait of the loop (the exit drain keeps kWaitLimitNs)
     int R;                // rows per CTA block (multiple of 4, <= kLoopMaxRows)
     int RS;               // column stride of a Y slice (R or R + 4, RS = 4 mod 8: see loop_slice_stride)
     int LC;               // Y columns per streamed chunk (multiple of 4)
@@ -137,6 +138,9 @@ struct YStream {
     bool loaded;        // the slice of this step is resident in the ring
     int64_t nloaded;
     bool* ok;
+    uint64_t wait_ns;
+    uint32_t nissued;   // chunks issued so far (consumer thread 0) and chunks waited: at exit the
+    uint32_t nwaited;   // ones in between are still landing in the ring
 };
 
 template <int NCONS, class Coef, class Body>
@@ -152,6 +156,7 @@ __device__ __forceinline__ void ystream(YStream& ys, int64_t k, int np, int tid,
         const int lc = (int)min((int64_t)ys.LC, k - l0);
         const uint32_t bytes = (uint32_t)lc * (uint32_t)ys.R * 4u;
         mbar_arrive_expect_tx(&ys.ybar[bf], (uint32_t)np * bytes);
+        ys.nissued = max(ys.nissued, ys.count + (uint32_t)c + 1u);
         for (int pl = 0; pl < np; ++pl)
             bulk_g2s(ys.ring + (size_t)bf * ys.buf_floats + (size_t)pl * plane,
                      ys.ysb_b + ((int64_t)pl * ys.d_max + l0) * ys.R, bytes, &ys.ybar[bf], ys.pol);
@@ -187,9 +192,13 @@ __device__ __forceinline__ void ystream(YStream& ys, int64_t k, int np, int tid,
         }
         const int bf = bufof(c);
         const uint32_t par = ((ys.count + (uint32_t)c) / (uint32_t)ys.NB) & 1u;
-        if (!reuse && *ys.ok && !mbar_wait(&ys.ybar[bf], par)) {
-            loop_abort(ctl, ys.bar, ST_ETIMEOUT);
-            *ys.ok = false;
+        if (!reuse && *ys.ok) {
+            if (mbar_wait(&ys.ybar[bf], par, ys.wait_ns)) {
+                ys.nwaited = max(ys.nwaited, ys.count + (uint32_t)c + 1u);
+            } else {
+                loop_abort(ctl, ys.bar, ST_ETIMEOUT);
+                *ys.ok = false;
+            }
         }
         const int64_t l0 = c * ys.LC;
         const int lc = (int)min((int64_t)ys.LC, k - l0);
@@ -287,6 +296,10 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     ys.loaded = false;
     ys.nloaded = 0;
     ys.ok = &ok;
+    ys.wait_ns = p.wait_ns;
+    ys.nissued = 0;
+    ys.nwaited = 0;
+    uint32_t iss_par = 0, iss_mask = 0;  // producer: parity and presence of the last issue into each stage
 
     // pass pipeline state (producer and consumers advance identical copies)
     int ps = 0;
@@ -445,7 +458,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             pf_ph0 = pph;
             int64_t g = L0 / NT, t = L0 - (L0 / NT) * NT;
             for (int64_t i = 0; i < npref; ++i) {
-                if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                if (preuse && !mbar_wait(&empty[ps], pph ^ 1u, p.wait_ns)) {
                     loop_abort(ctl, p.bar, ST_ETIMEOUT);
                     ok = false;
                     npref = i;
@@ -457,6 +470,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 mbar_arrive_expect_tx(&full[ps], x_bytes);
                 bulk_g2s(st + XI, planes + (g * p.group_stride + t * p.tile_stride) * Cfg::ESIZE, x_bytes, &full[ps],
                          pol_x);
+                iss_mask |= 1u << ps;
+                iss_par = (iss_par & ~(1u << ps)) | (pph << ps);
                 if (++ps == S) {
                     ps = 0;
                     pph ^= 1u;
@@ -518,7 +533,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             if (lane == 0) ctl->fro_last = sqrt(fmax(fs, 0.0));
         }
         if (k > 0) {
-            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;   // barrier 1
+            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl, p.wait_ns)) ok = false;   // barrier 1
             if (!ok) break;
             // ---------------- O2: h(l) = sum_b hpart[b](l), k / G coefficients per CTA ----------------
             if (warp < NW) {
@@ -531,7 +546,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                     if (lane == 0) p.h[l] = acc;
                 }
             }
-            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;   // barrier 2
+            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl, p.wait_ns)) ok = false;   // barrier 2
             if (!ok) break;
         }
 
@@ -564,7 +579,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 if (k > 0) block_dots(p.hpart);
             }
         }
-        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;  // barrier 3
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl, p.wait_ns)) ok = false;  // barrier 3
         if (!ok) break;
         if constexpr (!WT) {
             // every consumer is past O3, so the ring is free: the first X tiles of the pass (L2
@@ -638,7 +653,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                         if (lane == 0) p.h[l] = acc;
                     }
                 }
-                if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;  // barrier 3b
+                if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl, p.wait_ns)) ok = false;  // barrier 3b
                 if (!ok) break;
             }
             // ---------------- O5: z = u - Y g for this block's rows ----------------
@@ -649,7 +664,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             ystream_end_step(ys);
             __syncthreads();
             prefetch_x();
-            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;  // barrier 3c
+            if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl, p.wait_ns)) ok = false;  // barrier 3c
             if (!ok) break;
         }
 
@@ -684,7 +699,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                     }
                 }
                 for (int64_t i = npref; i < nunits; ++i) {
-                    if (preuse && !mbar_wait(&empty[ps], pph ^ 1u)) {
+                    if (preuse && !mbar_wait(&empty[ps], pph ^ 1u, p.wait_ns)) {
                         loop_abort(ctl, p.bar, ST_ETIMEOUT);
                         ok = false;
                         break;
@@ -699,6 +714,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                     mbar_arrive_expect_tx(&full[ps], WT ? 2u * xi_bytes : xi_bytes);
                     bulk_g2s(st, p.v2s + t * 2 * MT, xi_bytes, &full[ps], pol_xi);
                     if constexpr (WT) bulk_g2s(st + 2 * MT, p.zs + t * 2 * MT, xi_bytes, &full[ps], pol_xi);
+                    iss_mask |= 1u << ps;
+                    iss_par = (iss_par & ~(1u << ps)) | (pph << ps);
                     if (++ps == S) {
                         ps = 0;
                         pph ^= 1u;
@@ -773,7 +790,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                         if (cw < ncols) e_old[qq] = __ldcg(&p.e[c0 + cw]);
                     }
                 }
-                if (ok && !mbar_wait(&full[s], ph)) {
+                if (ok && !mbar_wait(&full[s], ph, p.wait_ns)) {
                     loop_abort(ctl, p.bar, ST_ETIMEOUT);
                     ok = false;
                 }
@@ -833,7 +850,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 p.pbest_j[b] = bj;
             }
         }
-        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl)) ok = false;  // barrier 4
+        if (!grid_sync(p.bar, (uint32_t)G, gen, &sflags[0], ctl, p.wait_ns)) ok = false;  // barrier 4
         if (!ok) break;
 
         // ---------------- A: argmax over CTAs, Frobenius residual ----------------
@@ -870,20 +887,25 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
     }
 
     // ---------------- leave: drain prefetched tiles, publish the final state ----------------
-    if (warp == NW && lane == 0 && npref > 0) {
-        // The loop stopped after the X tiles of the next pass were prefetched: complete those
-        // stages' phases (second arrival, no pivot-vector part) and wait for the X tiles to
-        // land, so that no bulk copy into this CTA's shared memory is in flight at exit.
-        for (int64_t i = 0; i < npref; ++i) {
-            const int64_t si = pf_s0 + i;
-            const int sp = (int)(si % S);
-            const uint32_t par = pf_ph0 ^ (uint32_t)((si / S) & 1);
-            mbar_arrive(&full[sp]);
-            if (!mbar_wait(&full[sp], par)) {
+    // No bulk copy may still be writing this CTA's shared memory when it exits, whether the loop
+    // ended normally or a wait gave up (RBD_ETIMEOUT): these waits keep the default bound.
+    if (warp == NW && lane == 0) {
+        // X tiles prefetched for a pass that did not run: their phases' second arrival (no
+        // pivot-vector part), then every stage whose last issue may still be in flight
+        for (int64_t i = 0; i < npref; ++i) mbar_arrive(&full[(int)((pf_s0 + i) % S)]);
+        for (int s = 0; s < S; ++s)
+            if (((iss_mask >> s) & 1u) && !mbar_wait(&full[s], (iss_par >> s) & 1u)) {
                 raise_status(ctl, ST_ETIMEOUT);
                 break;
             }
-        }
+    }
+    if (warp < NW && tid == 0) {
+        // Y chunks issued but never waited for (a wait gave up part-way through a stream)
+        for (uint32_t gc = ys.nwaited; gc < ys.nissued; ++gc)
+            if (!mbar_wait(&ybar[gc % (uint32_t)ys.NB], (gc / (uint32_t)ys.NB) & 1u)) {
+                raise_status(ctl, ST_ETIMEOUT);
+                break;
+            }
     }
     if (b == 0 && tid == 0) {
         if (stop != STOP_NONE) {
@@ -943,6 +965,7 @@ cudaError_t launch_loop(const Work& w, const void* X, double* Y, int64_t ldy, do
     p.W = w.W;
     p.KMAX = w.KMAX;
     p.evict_first = w.evict_first;
+    p.wait_ns = wait_limit_ns(kWaitLimitNs);
     p.X = X;
     p.Y = Y;
     p.T = T;

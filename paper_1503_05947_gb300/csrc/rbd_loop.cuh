@@ -52,7 +52,8 @@ __device__ __forceinline__ void loop_abort(Ctl* ctl, uint32_t* bar, int32_t st) 
 // nblocks * gen, so no CTA has to reset it and the last arrival needs no extra release step.
 // Returns false in all threads of a CTA whose wait ran out (RBD_ETIMEOUT) or that saw the abort
 // bit (the caller then leaves the loop).
-__device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint32_t& gen, int* s_ok, Ctl* ctl) {
+__device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint32_t& gen, int* s_ok, Ctl* ctl,
+                                          uint64_t limit_ns = kBarrierLimitNs) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -66,7 +67,7 @@ __device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint3
             while (true) {
                 v = ld_acquire_u32(bar);
                 if ((v & kAbortBit) || v >= target) break;
-                if (globaltimer_ns() - t0 > kBarrierLimitNs) {
+                if (globaltimer_ns() - t0 > limit_ns) {
                     loop_abort(ctl, bar, ST_ETIMEOUT);
                     v = kAbortBit;
                     break;

@@ -199,6 +199,9 @@ struct DeviceState {
     bool ready = false;
 };
 cudaError_t device_state(DeviceState& out);
+// The bound on device-side waits the next launches take: the caller's (rbd_set_wait_limit), or
+// dflt when none is set.
+uint64_t wait_limit_ns(uint64_t dflt);
 // cudaError_t -> rbd_status (allocation failures are RBD_ENOMEM, every other error RBD_ECUDA).
 rbd_status map_cuda(cudaError_t e);
 // The argument rules of rbd_compress (and of every entry point that takes its arguments).

@@ -118,6 +118,8 @@ def load():
     lib.rbd_project.argtypes = [_PTR, _I64, _I64, _I64, _PTR, ctypes.c_int, _I64, _I64, _PTR, _I64, _PTR]
     lib.rbd_set_profiling.restype = None
     lib.rbd_set_profiling.argtypes = [ctypes.c_int]
+    lib.rbd_set_wait_limit.restype = ctypes.c_uint64
+    lib.rbd_set_wait_limit.argtypes = [ctypes.c_uint64]
     lib.rbd_get_profile.restype = ctypes.c_int
     lib.rbd_get_profile.argtypes = [ctypes.POINTER(_Profile)]
     lib.rbd_status_string.restype = ctypes.c_char_p
@@ -441,6 +443,12 @@ def project(Y: torch.Tensor, V: torch.Tensor, out: Optional[torch.Tensor] = None
 
 def set_profiling(enabled: bool):
     load().rbd_set_profiling(1 if enabled else 0)
+
+
+def set_wait_limit(ns: int) -> int:
+    """Bound (nanoseconds) on every device-side wait of the persistent kernels launched from now
+    on; 0 restores the defaults.  Returns the previous setting."""
+    return int(load().rbd_set_wait_limit(int(ns)))
 
 
 def get_profile() -> dict:

@@ -120,3 +120,12 @@ def test_no_cpu_fallback_in_product_path():
         if fn.endswith(".py"):
             txt = open(os.path.join(pkg, fn)).read()
             assert "import oracle" not in txt and "from oracle" not in txt, fn
+
+
+def test_wait_limit_setting_round_trips(lib):
+    # host-only: the bound on device-side waits is a process-wide setting (0 = the defaults)
+    prev = rbd.set_wait_limit(5000)
+    try:
+        assert rbd.set_wait_limit(0) == 5000
+    finally:
+        rbd.set_wait_limit(prev)
