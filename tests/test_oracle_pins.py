@@ -56,6 +56,31 @@ def test_project_and_reconstruct(oracle_mod):
     assert np.abs(oracle_mod.reconstruct(Y, T) - Y @ T).max() <= 1e-14
 
 
+@pytest.mark.parametrize("r", [1, 5, 17])
+def test_reconstruct_exact_recovery(oracle_mod, r):
+    """Uncompress (Section 3.1) after Algorithm 1 on a rank-r matrix stops at d = r: Y T is X
+    itself, up to rounding (Y spans the column space exactly)."""
+    X = gen.lowrank_haar(90, 70, np.linspace(2.0, 0.5, r), seed=100 + r)
+    res = oracle_mod.compress(X, 1e-12, 40)
+    assert res["d"] == r
+    Xr = oracle_mod.reconstruct(res["Y"], res["T"])
+    assert np.abs(Xr - X).max() <= 1e-13 * np.abs(X).max()
+
+
+def test_reconstruct_of_projection_is_identity_on_span(oracle_mod):
+    """For v in span(Y), the out-of-sample map followed by uncompress returns v: Y (Y' v) = v."""
+    X = gen.decay_matrix_c1(seed=5, m=150, n=80)
+    Y = oracle_mod.compress(X, 0.0, 24)["Y"]
+    rng = np.random.default_rng(7)
+    V = np.asfortranarray(Y @ rng.standard_normal((24, 9)))
+    back = oracle_mod.reconstruct(Y, oracle_mod.project(Y, V))
+    assert np.abs(back - V).max() <= 1e-13 * np.abs(V).max()
+    # and for any v, the residual v - Y Y'v is orthogonal to Y (Galerkin): Y'(v - Y Y' v) = 0
+    W = gen.out_of_sample(150, 5, seed=11)
+    R = W - oracle_mod.reconstruct(Y, oracle_mod.project(Y, W))
+    assert np.abs(oracle_mod.project(Y, R)).max() <= 1e-14 * np.abs(W).max() * 150
+
+
 def test_invalid_arguments(oracle_mod):
     X = np.ones((4, 3), order="F")
     for kw in (dict(tol=-1.0, d_max=2), dict(tol=0.0, d_max=0), dict(tol=0.0, d_max=4),
