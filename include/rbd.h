@@ -47,7 +47,14 @@ typedef enum rbd_status {
 typedef enum rbd_dtype {
     RBD_F64 = 0,
     RBD_F32 = 1,
-    RBD_BF16 = 2
+    RBD_BF16 = 2,
+    /* FP32 storage whose fused pass sums each tile's products in FP32 and folds the sum into an
+       FP64-grade accumulator once per tile (as BF16 storage does): the precision form with FP32
+       accumulation.  The orthogonalisation, the running indicator and the certified E_cur stay
+       FP64-grade; T(k, j) carries the FP32 accumulation error (~2^-20 ||X(:, j)||), so pivots
+       near a tie may differ from an FP64 run's.  RBD_F32 keeps FP64-grade dot products.
+       rbd_compress and its device-buffer variants (not the weighted, batched or stepwise paths). */
+    RBD_F32_ACC32 = 3
 } rbd_dtype;
 
 /* How the tolerance `tol` of Algorithm 1 (epsilon_R) is applied. */
@@ -60,7 +67,14 @@ typedef enum rbd_tol_mode {
     /* step 2.4 stops when ||X - Y T||_F <= tol * ||X||_F (the Frobenius error is the square
        root of the sum of the per-column squared residuals); step 2.2 breaks when
        ||v|| < tol * ||X||_F / sqrt(n). */
-    RBD_TOL_FRO_REL = 2
+    RBD_TOL_FRO_REL = 2,
+    /* no tolerance: exactly d_max bases.  Neither step 2.4's test nor step 2.2's break (nor the
+       numerical-rank floor) applies; only an orthogonalised vector that is zero or not finite
+       stops the loop.  A measurement mode (every pass streams X once whatever the data): past
+       X's numerical rank the bases are rounding noise and carry no information.  It runs in the
+       four-barrier loop kernel (which forms ||v|| from the orthogonalised vector itself), so
+       not with RBD_F32_ACC32; not taken by the batched form. */
+    RBD_TOL_NONE = 3
 } rbd_tol_mode;
 
 /* Why the greedy loop ended. */

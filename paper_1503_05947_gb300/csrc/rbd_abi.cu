@@ -35,7 +35,7 @@ static bool classic_loop_forced() {
 
 
 bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms,
-               int pass_ctas_per_sm, int loop_max_smem, int wt) {
+               int pass_ctas_per_sm, int loop_max_smem, int wt, bool allow_defer) {
     w = Work{};
     w.wt = wt;
     w.m = m;
@@ -84,7 +84,8 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
             const int KC = (int)round_up(d_max, 4);
             const int LCd = defer_chunk_cols(xt, (int)RS);
             const size_t smd = defer_smem_bytes(xt, (int)R, KC);
-            if (w.use_loop && !wt && !classic_loop_forced() && LCd >= 4 && smd > 0 && smd <= (size_t)loop_max_smem) {
+            if (w.use_loop && !wt && allow_defer && !classic_loop_forced() && LCd >= 4 && smd > 0 &&
+                smd <= (size_t)loop_max_smem) {
                 w.use_defer = 1;
                 w.KC = KC;
                 w.LC = LCd;
@@ -309,7 +310,8 @@ rbd_status map_cuda(cudaError_t e) {
     return RBD_ECUDA;
 }
 
-static bool valid_dtype(int t) { return t == RBD_F64 || t == RBD_F32 || t == RBD_BF16; }
+static bool valid_dtype(int t) { return t == RBD_F64 || t == RBD_F32 || t == RBD_BF16 || t == RBD_F32_ACC32; }
+
 
 // ---------------------------------------------------------------------------------------
 // The greedy loop on device buffers
@@ -325,11 +327,15 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
     DeviceState ds;
     cudaError_t ce = device_state(ds);
     if (ce != cudaSuccess) return map_cuda(ce);
+    const bool acc32 = xt == RBD_F32_ACC32;
+    xt = (rbd_dtype)storage_of((int)xt);
     Work w;
     if (!plan_work(w, m, n, ldx, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem,
-                   wts ? 1 : 0))
+                   wts ? 1 : 0, mode != RBD_TOL_NONE))
         return RBD_EUNSUPPORTED;
     if (xt == RBD_BF16 && !w.use_loop) return RBD_EUNSUPPORTED;  // BF16 runs in the persistent kernel only
+    if (acc32 && (!w.use_defer || wts)) return RBD_EUNSUPPORTED;  // FP32 accumulation: the two-barrier kernel
+    w.acc32 = acc32 ? 1 : 0;
     if (wts && (!w.use_loop || k0 > 0)) return RBD_EUNSUPPORTED;  // the A-norm form: loop kernel, fresh runs
     w.wts = wts;
 
@@ -501,7 +507,7 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
             pf.loop_launches = 1;
             pf.pass_launches = dd;  // fused passes executed inside the loop kernel
         }
-        pf.pass_bytes = pf.pass_launches * m * n * (xt == RBD_F64 ? 8 : (xt == RBD_F32 ? 4 : 2));
+        pf.pass_bytes = pf.pass_launches * m * n * elem_bytes((int)xt);
         pf.loop_kernel = w.use_loop;
         cudaGetLastError();
         t_profile = pf;
@@ -530,7 +536,8 @@ rbd_status validate(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t l
     if (d_max > m || d_max > n) return RBD_EINVAL;
     if (start < 0 || start >= n) return RBD_EINVAL;
     if (!(tol >= 0.0) || tol == __builtin_inf()) return RBD_EINVAL;
-    if (mode != RBD_TOL_MAXCOL_ABS && mode != RBD_TOL_MAXCOL_REL && mode != RBD_TOL_FRO_REL) return RBD_EINVAL;
+    if (mode != RBD_TOL_MAXCOL_ABS && mode != RBD_TOL_MAXCOL_REL && mode != RBD_TOL_FRO_REL && mode != RBD_TOL_NONE)
+        return RBD_EINVAL;
     if (m > (int64_t(1) << 40) || n > (int64_t(1) << 40)) return RBD_EUNSUPPORTED;
     return RBD_OK;
 }
@@ -543,6 +550,7 @@ extern "C" {
 
 size_t rbd_compress_workspace_bytes(int64_t m, int64_t n, int64_t d_max, rbd_dtype xt) {
     if (m < 1 || n < 1 || d_max < 1 || d_max > m || d_max > n || !valid_dtype((int)xt)) return 0;
+    xt = (rbd_dtype)storage_of((int)xt);
     DeviceState ds;
     if (device_state(ds) != cudaSuccess) {
         // no device: the larger of the two paths' needs, planned for a 160-SM part
@@ -601,7 +609,7 @@ rbd_status rbd_compress_rows(const void* X, rbd_dtype xt, int64_t m, int64_t n, 
     cudaError_t ce = device_state(ds);
     if (ce != cudaSuccess) return map_cuda(ce);
     cudaStream_t st = (cudaStream_t)stream;
-    const int es = (xt == RBD_F64) ? 8 : (xt == RBD_F32 ? 4 : 2);
+    const int es = elem_bytes((int)xt);
     void* Xt = nullptr;
     ce = cudaMallocAsync(&Xt, (size_t)m * (size_t)n * es, st);
     if (ce != cudaSuccess) {
@@ -630,7 +638,7 @@ rbd_status rbd_compress_host(const void* X, rbd_dtype xt, int64_t m, int64_t n, 
     rbd_status v = validate(X, xt, m, n, ldx, tol, mode, d_max, start, Y, ldy, T, ldt, pivots, err);
     if (v != RBD_OK) return v;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t es = (xt == RBD_F64) ? 8 : (xt == RBD_F32 ? 4 : 2);
+    const size_t es = (size_t)elem_bytes((int)xt);
     // device copies: X with its leading dimension m, outputs with compact leading dimensions
     void *dX = nullptr, *dY = nullptr, *dT = nullptr, *dP = nullptr, *dE = nullptr, *dN = nullptr;
     cudaError_t ce = cudaMallocAsync(&dX, (size_t)m * n * es, st);

@@ -557,6 +557,9 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             nu2 = warp_sum_double(nu2);
             fs = warp_sum_double(fs);
             if (lane == 0) {
+                // nu^2 = ||v1||^2 - ||h||^2 (accurate while ||h|| << ||v1||, which the numerical-rank
+                // floor guarantees: past it both are rounding noise, and the no-tolerance mode that
+                // runs there takes the four-barrier kernel)
                 const double nuv = sqrt(fmax(nu2 - hh, 0.0));
                 const double frol = sqrt(fmax(fs, 0.0));
                 const double xin = sqrt(xn2p);
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     }
                 }
                 if (st == STOP_NONE && k >= p.d_max) st = STOP_DMAX;
-                if (st == STOP_NONE && (nuv < eps_r22 || nuv <= kRankFloor * xin)) st = STOP_BREAK;
+                if (st == STOP_NONE && (nuv < eps_r22 || !(nuv > rank_floor_of(mode) * xin))) st = STOP_BREAK;
                 bcast[0] = nuv;
                 bcast[1] = recip_pos(nuv);
                 bcast[2] = hh;
@@ -741,6 +744,11 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                                 consume_tile_bf16<CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
                             else
                                 consume_tile_bf16<CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c);
+                        } else if constexpr (XT == 3) {
+                            if (rows == MT)
+                                consume_tile_f32acc<CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
+                            else
+                                consume_tile_f32acc<CPW, MT, false>(st, rows, warp, lane, acc_s, acc_c);
                         } else {
                             if (rows == MT)
                                 consume_tile<Cfg::PL, CPW, MT, true>(st, MT, warp, lane, acc_s, acc_c);
@@ -1036,14 +1044,15 @@ int defer_chunk_cols(int xt, int RS) {
     return lc < 252 ? lc : 252;
 }
 
+// xt 0..2: the storage type; 3: FP32 storage with FP32 accumulation in the pass
 static const void* defer_fn(int xt) {
     return (xt == 0) ? (const void*)defer_kernel<0> : (xt == 1) ? (const void*)defer_kernel<1>
-                                                                : (const void*)defer_kernel<2>;
+         : (xt == 2) ? (const void*)defer_kernel<2> : (const void*)defer_kernel<3>;
 }
 
 cudaError_t defer_kernel_setup(int max_smem) {
     cudaError_t e = cudaSuccess;
-    for (int xt = 0; xt < 3 && e == cudaSuccess; ++xt)
+    for (int xt = 0; xt < 4 && e == cudaSuccess; ++xt)
         e = cudaFuncSetAttribute(defer_fn(xt), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     return e;
 }
@@ -1098,8 +1107,8 @@ cudaError_t launch_defer(const Work& w, const void* X, double* Y, int64_t ldy, d
     void* args[] = {&p};
     const int threads =
         32 + ((w.xt == 0) ? TileCfg<0>::THREADS : (w.xt == 1) ? TileCfg<1>::THREADS : TileCfg<2>::THREADS);
-    return cudaLaunchCooperativeKernel(defer_fn(w.xt), dim3((unsigned)w.G_loop), dim3((unsigned)threads), args,
-                                       w.loop_smem, st);
+    return cudaLaunchCooperativeKernel(defer_fn((w.xt == 1 && w.acc32) ? 3 : w.xt), dim3((unsigned)w.G_loop),
+                                       dim3((unsigned)threads), args, w.loop_smem, st);
 }
 
 }  // namespace rbd

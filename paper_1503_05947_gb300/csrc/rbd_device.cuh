@@ -25,11 +25,17 @@ namespace rbd {
 enum : int32_t { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENONFINITE = 4,
                  ST_ETIMEOUT = 5, ST_EUNSUPPORTED = 6 };
 enum : int32_t { STOP_NONE = 0, STOP_TOL = 1, STOP_BREAK = 2, STOP_DMAX = 3 };
-enum : int32_t { MODE_MAXCOL_ABS = 0, MODE_MAXCOL_REL = 1, MODE_FRO_REL = 2 };
+enum : int32_t { MODE_MAXCOL_ABS = 0, MODE_MAXCOL_REL = 1, MODE_FRO_REL = 2, MODE_NONE = 3 };
+
 
 // Step 2.2 treats a pivot whose orthogonalised norm is at most kRankFloor * ||X(:, i)|| as
 // already in span(Y) (numerical-rank floor; matches RBD_RANK_FLOOR in rbd.h).
 constexpr double kRankFloor = 1e-12;
+
+// The numerical-rank floor of step 2.2's break test in a tolerance mode (none without a tolerance:
+// the loop then runs to d_max, stopping only on an orthogonalised vector that is zero or not
+// finite).
+__host__ __device__ __forceinline__ double rank_floor_of(int32_t mode) { return (mode == MODE_NONE) ? 0.0 : kRankFloor; }
 
 // Upper bound on any device-side wait (nanoseconds of %globaltimer).
 constexpr uint64_t kWaitLimitNs = 2000000000ull;

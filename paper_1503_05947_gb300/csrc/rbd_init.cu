@@ -160,6 +160,11 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
             ctl->fro_tol = p.tol * fro;  // compared with sqrt(sum of e_j)
             ctl->eps_r = -1.0;
             ctl->eps_r22 = p.tol * fro / sqrt((double)p.n);
+        } else if (p.mode == MODE_NONE) {
+            // no tolerance: exactly d_max bases (a measurement mode)
+            ctl->fro_tol = -1.0;
+            ctl->eps_r = -1.0;
+            ctl->eps_r22 = -1.0;
         } else {
             const double eps = (p.mode == MODE_MAXCOL_REL) ? p.tol * maxcol : p.tol;
             ctl->fro_tol = -1.0;

@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                     }
                 }
                 if (st == STOP_NONE && k >= p.d_max) st = STOP_DMAX;
-                if (st == STOP_NONE && (nea < eps_r22 || nuv <= kRankFloor * xin)) st = STOP_BREAK;
+                if (st == STOP_NONE && (nea < eps_r22 || !(nuv > rank_floor_of(mode) * xin))) st = STOP_BREAK;
                 bcast[0] = nuv;
                 const double inv = recip_pos(nuv);
                 bcast[1] = inv;                                   // once, for every thread of the pass

@@ -72,10 +72,15 @@ extern "C" rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t 
         cudaGetLastError();
         return map_cuda(ce);
     }
+    const bool acc32 = xt == RBD_F32_ACC32;
+    xt = (rbd_dtype)storage_of((int)xt);
     Work w;
-    if (!plan_work(w, m, n, ldx, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem))
+    if (!plan_work(w, m, n, ldx, d_max, (int)xt, ds.num_sms, ds.pass_ctas_per_sm[(int)xt], ds.loop_max_smem, 0,
+                   mode != RBD_TOL_NONE))
         return RBD_EUNSUPPORTED;
     if (xt == RBD_BF16 && !w.use_loop) return RBD_EUNSUPPORTED;
+    if (acc32 && !w.use_defer) return RBD_EUNSUPPORTED;
+    w.acc32 = acc32 ? 1 : 0;
     // the problem's workspace must fit the fixed array
     if (w.total_bytes > (size_t)RBD_NOALLOC_SCRATCH_BYTES) return RBD_ENOMEM;
     carve_work(w, scratch);

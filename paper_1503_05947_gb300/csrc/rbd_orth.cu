@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) orth_gemv_n_kernel(GemvNParams p) {
             }
             if (stop == STOP_NONE && k >= ctl->d_max) stop = STOP_DMAX;
             // step 2.2: break if ||v|| < eps_R, or below the numerical-rank floor
-            if (stop == STOP_NONE && (nu < ctl->eps_r22 || nu <= kRankFloor * xin)) stop = STOP_BREAK;
+            if (stop == STOP_NONE && (nu < ctl->eps_r22 || !(nu > rank_floor_of(ctl->mode) * xin))) stop = STOP_BREAK;
             if (stop != STOP_NONE) {
                 ctl->stop = stop;
                 if (p.progress) {

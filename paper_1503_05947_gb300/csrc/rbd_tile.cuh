@@ -171,6 +171,42 @@ __device__ __forceinline__ void consume_tile_bf16(const float* __restrict__ st, 
     }
 }
 
+// FP32 storage with FP32 accumulation (RBD_F32_ACC32, the precision form): FP32 products of the
+// stored values with the leading FP32 part of the pivot vector, summed in FP32 over the unit's rows
+// (8 per lane) and folded into the float-float accumulator once per unit.  Stage layout as for
+// consume_tile with one plane.
+template <int CPW, int MT, bool FULL>
+__device__ __forceinline__ void consume_tile_f32acc(const float* __restrict__ st, int rows, int warp, int lane,
+                                                    float (&acc_s)[CPW][4], float (&acc_c)[CPW][4]) {
+    constexpr int XI = 2 * MT;
+    const int R = FULL ? MT : rows;
+    const int nsl = FULL ? MT / 128 : (rows >> 7);
+    float part[CPW][4];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) part[q][e] = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < MT / 128; ++sl) {
+        if (!FULL && sl >= nsl) break;
+        const int off = sl * 128 + lane * 4;
+        const float4 zh = *reinterpret_cast<const float4*>(st + off);
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+            const float4 a = *reinterpret_cast<const float4*>(st + XI + (warp * CPW + q) * R + off);
+            part[q][0] = __fmaf_rn(a.x, zh.x, part[q][0]);
+            part[q][1] = __fmaf_rn(a.y, zh.y, part[q][1]);
+            part[q][2] = __fmaf_rn(a.z, zh.z, part[q][2]);
+            part[q][3] = __fmaf_rn(a.w, zh.w, part[q][3]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+        const float sum = __fadd_rn(__fadd_rn(part[q][0], part[q][1]), __fadd_rn(part[q][2], part[q][3]));
+        ff_add(acc_s[q][0], acc_c[q][0], sum, 0.f);
+    }
+}
+
 // BF16 storage in the A-norm form: as consume_tile_bf16, a second FP32 sum with the leading part
 // of z (stage layout of consume_tile_w).
 template <int CPW, int MT, bool FULL>

@@ -119,6 +119,10 @@ struct TileCfg<2> {
 
 // The diagonal A-norm form (Section 3.2) streams a second pivot-vector tile per unit: the stage
 // holds [xi hi | xi lo | z hi | z lo] (2 * MT floats each pair) ahead of the X tile.
+// RBD_F32_ACC32: FP32 storage (the planes and tiles of TileCfg<1>), FP32 accumulation per tile.
+template <>
+struct TileCfg<3> : TileCfg<1> {};
+
 template <int XT>
 struct TileCfgW : TileCfg<XT> {
     static constexpr int XI_FLOATS = 4 * TileCfg<XT>::MT;
@@ -156,6 +160,7 @@ struct Work {
     int LC;                 // Y columns per streamed chunk
     size_t loop_smem;       // dynamic shared memory bytes
     int use_defer;          // A = I: the two-barrier loop kernel (rbd_defer.cu) instead of rbd_loop.cu's
+    int acc32;              // RBD_F32_ACC32 (xt is then RBD_F32): FP32 accumulation in the pass
     int KC;                 // d_max rounded up to 4 (coefficient and T-block rows in shared memory)
     // regions
     Ctl* ctl;
@@ -184,8 +189,10 @@ struct Work {
 // loop_max_smem > 0 allows the persistent loop kernel with at most that much shared memory.
 // wt = 1 plans the loop kernel of the A-norm form (larger pass stages); the workspace layout
 // does not depend on wt.
+// allow_defer = false keeps the four-barrier loop kernel for A = I (the no-tolerance mode, whose
+// bases past the numerical rank need nu from v2 itself).
 bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt, int num_sms,
-               int pass_ctas_per_sm, int loop_max_smem, int wt = 0);
+               int pass_ctas_per_sm, int loop_max_smem, int wt = 0, bool allow_defer = true);
 // Carve the regions of `w` out of `base` (at least w.total_bytes, 256-byte aligned).
 void carve_work(Work& w, void* base);
 
@@ -199,6 +206,10 @@ struct DeviceState {
     bool ready = false;
 };
 cudaError_t device_state(DeviceState& out);
+// The storage type of X (RBD_F32_ACC32 stores FP32) and its element size.
+inline int storage_of(int t) { return (t == RBD_F32_ACC32) ? (int)RBD_F32 : t; }
+inline int elem_bytes(int t) { return (t == RBD_F64) ? 8 : (t == RBD_BF16) ? 2 : 4; }
+
 // The bound on device-side waits the next launches take: the caller's (rbd_set_wait_limit), or
 // dflt when none is set.
 uint64_t wait_limit_ns(uint64_t dflt);

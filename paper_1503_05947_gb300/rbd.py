@@ -22,7 +22,7 @@ from . import buildlib as _build
 _I64, _DBL, _PTR = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
 DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
-TOL_MODES = {"maxcol_abs": 0, "maxcol_rel": 1, "fro_rel": 2}
+TOL_MODES = {"maxcol_abs": 0, "maxcol_rel": 1, "fro_rel": 2, "none": 3}
 STOP_REASONS = {0: "none", 1: "tol", 2: "break", 3: "d_max"}
 RANK_FLOOR = 1e-12
 
@@ -187,16 +187,31 @@ def workspace_bytes(m: int, n: int, d_max: int, dtype=torch.float64) -> int:
     return int(load().rbd_compress_workspace_bytes(m, n, d_max, DTYPES[dtype]))
 
 
+def _xt(X: torch.Tensor, accumulate: str) -> int:
+    """rbd_dtype of X: its storage type, and for float32 the pass's accumulation ("exact": FP64-grade
+    float-float dot products; "fp32": FP32 sums per tile, RBD_F32_ACC32)."""
+    if X.dtype not in DTYPES:
+        raise ValueError(f"unsupported dtype {X.dtype}")
+    if accumulate == "fp32":
+        if X.dtype != torch.float32:
+            raise ValueError('accumulate="fp32" applies to float32 storage')
+        return 3
+    if accumulate != "exact":
+        raise ValueError(f"unknown accumulate {accumulate!r}")
+    return DTYPES[X.dtype]
+
+
 def compress(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: str = "maxcol_abs",
-             workspace: Optional[torch.Tensor] = None, weights: Optional[torch.Tensor] = None) -> Compressed:
+             workspace: Optional[torch.Tensor] = None, weights: Optional[torch.Tensor] = None,
+             accumulate: str = "exact") -> Compressed:
     """Algorithm 1 on a column-major CUDA tensor X (m x n) of dtype float64/float32/bfloat16.
     With ``weights`` (m positive float64 values on X's device) the error is measured in the
-    A-norm of A = diag(weights) (Section 3.2; rbd_compress_weighted)."""
+    A-norm of A = diag(weights) (Section 3.2; rbd_compress_weighted).  ``accumulate="fp32"``
+    (float32 X only) sums the pass's products in FP32 per tile (RBD_F32_ACC32)."""
     lib = load()
     if not X.is_cuda:
         raise ValueError("X must be a CUDA tensor (use compress_host for host arrays)")
-    if X.dtype not in DTYPES:
-        raise ValueError(f"unsupported dtype {X.dtype}")
+    xt = _xt(X, accumulate)
     m, n = X.shape
     ldx = _colmajor(X, "X")
     dev = X.device
@@ -215,12 +230,12 @@ def compress(X: torch.Tensor, tol: float, d_max: int, start: int = 0, tol_mode: 
     res = _Result()
     with torch.cuda.device(dev):
         if weights is None:
-            st = lib.rbd_compress(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, float(tol), TOL_MODES[tol_mode],
+            st = lib.rbd_compress(X.data_ptr(), xt, m, n, ldx, float(tol), TOL_MODES[tol_mode],
                                   int(d_max), int(start), Y.data_ptr(), m, T.data_ptr(), d_max, piv.data_ptr(),
                                   err.data_ptr(), nu.data_ptr(), ws_ptr, ws_bytes, _stream_ptr(dev),
                                   ctypes.byref(res))
         else:
-            st = lib.rbd_compress_weighted(X.data_ptr(), DTYPES[X.dtype], m, n, ldx, weights.data_ptr(), float(tol),
+            st = lib.rbd_compress_weighted(X.data_ptr(), xt, m, n, ldx, weights.data_ptr(), float(tol),
                                            TOL_MODES[tol_mode], int(d_max), int(start), Y.data_ptr(), m,
                                            T.data_ptr(), d_max, piv.data_ptr(), err.data_ptr(), nu.data_ptr(),
                                            ws_ptr, ws_bytes, _stream_ptr(dev), ctypes.byref(res))

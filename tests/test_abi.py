@@ -81,7 +81,7 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     assert call(start=-1) == 1
     assert call(tol=-1.0) == 1
     assert call(tol=float("nan")) == 1
-    assert call(mode=3) == 1
+    assert call(mode=4) == 1
     assert call(xt=7) == 1
     assert call(ldt=3) == 1
     # the A-norm form: the same checks, plus a NULL or misaligned weight vector

@@ -177,3 +177,28 @@ def test_workspace_supplied_by_caller(oracle_mod):
     with pytest.raises(rbd.RbdError) as ei:
         rbd.compress(to_device(X), 0.0, 32, workspace=small)
     assert ei.value.status == 2
+
+
+@pytest.mark.parametrize("xt", [torch.float64, torch.float32], ids=["fp64", "fp32"])
+def test_no_tolerance_mode_runs_to_d_max(oracle_mod, xt):
+    """tol_mode "none" (a measurement mode): exactly d_max bases past the numerical rank of X, with
+    finite outputs; up to that rank, the oracle's bases (a run that breaks there)."""
+    import paper_1503_05947_gb300 as rbd
+    Xt = to_device(gen.lowrank_haar(3000, 900, 2.0 ** (-0.5 * np.arange(20)), seed=21), xt)
+    Xs = to_numpy(Xt)
+    b = rbd.compress(Xt, 0.0, 40, tol_mode="none")
+    assert b.d == 40 and b.stop_reason == "d_max"
+    assert torch.isfinite(b.Y).all() and torch.isfinite(b.T).all() and torch.isfinite(b.err).all()
+    ref = oracle_mod.compress(Xs, 0.0, 40)
+    # the bases before the orthogonalised pivots reach rounding level (nu >= 1e-4 ||x_i||; FP32
+    # storage rounding keeps the oracle going to d_max, past the 20 significant directions)
+    cond = ref["nu"] / np.linalg.norm(Xs[:, ref["pivots"]], axis=0)
+    k = int(np.argmax(cond < 1e-4)) if (cond < 1e-4).any() else ref["d"]
+    assert 18 <= k <= 24
+    # (err[k - 1] is the residual of the next pivot, already at rounding level: not compared)
+    cut = {key: (v[:, :k] if key == "Y" else v[:k]) for key, v in ref.items() if key in ("Y", "T", "pivots", "nu")}
+    cut["err"] = ref["err"][:k - 1]
+    cut["d"] = k
+    got = {"Y": to_numpy(b.Y[:, :k]), "T": to_numpy(b.T[:k]), "pivots": b.pivots[:k].cpu().numpy(),
+           "err": b.err[:k - 1].cpu().numpy(), "nu": b.nu[:k].cpu().numpy(), "d": k}
+    assert_parity(Xs, cut, got, what="no-tolerance run up to the rank")

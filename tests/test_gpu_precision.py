@@ -42,8 +42,8 @@ def _stored(Xn, dtype):
     return X, to_numpy(X)
 
 
-def _run(rbd, X, tol, d_max, mode="maxcol_abs", start=0):
-    r = rbd.compress(X, tol, d_max, start=start, tol_mode=mode)
+def _run(rbd, X, tol, d_max, mode="maxcol_abs", start=0, accumulate="exact"):
+    r = rbd.compress(X, tol, d_max, start=start, tol_mode=mode, accumulate=accumulate)
     return {"Y": to_numpy(r.Y), "T": to_numpy(r.T), "pivots": r.pivots.cpu().numpy(),
             "err": r.err.cpu().numpy(), "nu": r.nu.cpu().numpy(), "d": r.d, "next": r.next_pivot,
             "stop": r.stop_reason}
@@ -129,6 +129,54 @@ def test_bf16_storage_invariants(rbd, oracle_mod, case):
     got = _run(rbd, X, tol, d_max, mode)
     ref = oracle_mod.compress(Xs, tol, d_max, 0, mode)
     _bf16_checks(Xs, got, ref, what=f"BF16 {name}")
+
+
+# ------------------------------------------- FP32 storage, FP32 accumulation (RBD_F32_ACC32)
+ACC32_CASES = [
+    ("parametric 4096x1024", lambda: gen.parametric_snapshots(4096, 1024, seed=2), 1e-5, 48, "maxcol_rel"),
+    ("decay 2048x600", lambda: gen.lowrank_haar(2048, 600, 2.0 ** (-np.arange(200) / 8), seed=8), 1e-4, 64,
+     "maxcol_rel"),
+    ("ragged 1000x333 fro", lambda: gen.decay_matrix_c1(seed=9, noise_sigma=1e-4, m=1000, n=333), 1e-4, 40,
+     "fro_rel"),
+]
+
+
+@pytest.mark.parametrize("case", ACC32_CASES, ids=[c[0] for c in ACC32_CASES])
+def test_fp32_accumulation_invariants(rbd, oracle_mod, case):
+    """The precision form with FP32 accumulation: per-tile FP32 sums of 8 products per lane, so T
+    carries ~2^-20 relative error and pivots are not pinned to the oracle's; the invariants that
+    still hold exactly are checked as for BF16 storage, on the same stored values."""
+    name, build, tol, d_max, mode = case
+    X, Xs = _stored(np.asfortranarray(build()), torch.float32)
+    got = _run(rbd, X, tol, d_max, mode, accumulate="fp32")
+    ref = oracle_mod.compress(Xs, tol, d_max, 0, mode)
+    _bf16_checks(Xs, got, ref, what=f"FP32-acc {name}")
+
+
+def test_fp32_accumulation_against_exact_form(rbd):
+    """While the columns' residuals stay above the running indicator's FP32 floor (T is accurate to
+    ~1e-8 ||x_j||, so e_j = ||x_j||^2 - sum T^2 carries ~2e-8 ||x_j||^2; here d <= 8, relative
+    residual ~6e-5), FP32 accumulation picks the same pivots as the FP64-grade form and reconstructs
+    X as well at equal d.  Past that floor its pivots follow the indicator's rounding (the certified
+    E_cur stays exact, the basis converges more slowly)."""
+    X, Xs = _stored(np.asfortranarray(gen.parametric_snapshots(4096, 1024, seed=2)), torch.float32)
+    for d in (4, 6, 8):
+        a = _run(rbd, X, 0.0, d)
+        b = _run(rbd, X, 0.0, d, accumulate="fp32")
+        assert a["d"] == b["d"] == d and np.array_equal(a["pivots"], b["pivots"])
+        ea = np.linalg.norm(Xs - a["Y"] @ a["T"])
+        eb = np.linalg.norm(Xs - b["Y"] @ b["T"])
+        assert abs(eb - ea) <= 1e-3 * ea, (d, ea, eb)
+        dT = np.abs(b["T"] - b["Y"].T @ Xs) / np.linalg.norm(Xs, axis=0)[None, :]
+        assert dT.max() <= 5e-8, dT.max()
+
+
+def test_fp32_accumulation_rejected_where_unsupported(rbd):
+    X, _ = _stored(np.asfortranarray(gen.parametric_snapshots(512, 256, seed=2)), torch.float32)
+    with pytest.raises(rbd.RbdError):
+        rbd.compress(X, 0.0, 8, weights=torch.ones(512, dtype=torch.float64, device="cuda"), accumulate="fp32")
+    with pytest.raises(ValueError):
+        rbd.compress(X.double(), 0.0, 8, accumulate="fp32")
 
 
 def test_bf16_deterministic(rbd):
