@@ -25,30 +25,41 @@ _lock = threading.Lock()
 _libs: dict = {}
 
 
-def _so_path(mutant: int) -> str:
+def _so_path(mutant: int, omp: bool = False) -> str:
     name = "librbd_oracle.so" if mutant == 0 else f"librbd_oracle_mut{mutant}.so"
+    if omp:
+        name = "librbd_oracle_omp.so"
     return os.path.join(_BUILD, name)
 
 
-def build(mutant: int = 0, force: bool = False) -> str:
-    """Compile the oracle (optionally with a planted mistake, for pin tests) with gcc."""
-    out = _so_path(mutant)
+def build(mutant: int = 0, force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle (optionally with a planted mistake, for pin tests) with gcc.  omp=True
+    builds the same source with OpenMP (its independent column loops on several threads, the
+    same arithmetic per column and the same column-order reductions): the all-core CPU baseline."""
+    out = _so_path(mutant, omp)
     if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
         return out
     os.makedirs(_BUILD, exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared",
            f"-DRBD_ORACLE_MUTANT={int(mutant)}", _SRC, "-o", tmp, "-lm"]
+    if omp:
+        cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
 
 
-def load(mutant: int = 0):
+def load(mutant: int = 0, omp: bool = False):
+    key = ("omp", 0) if omp else mutant
     with _lock:
-        if mutant in _libs:
-            return _libs[mutant]
-        lib = ctypes.CDLL(build(mutant))
+        if key in _libs:
+            return _libs[key]
+        lib = ctypes.CDLL(build(mutant, omp=omp))
+        lib.rbd_oracle_set_threads.restype = None
+        lib.rbd_oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.rbd_oracle_threads.restype = ctypes.c_int
+        lib.rbd_oracle_threads.argtypes = []
         i64, dbl, ptr = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
         lib.rbd_oracle_compress.restype = ctypes.c_int
         lib.rbd_oracle_compress.argtypes = [ptr, i64, i64, i64, dbl, ctypes.c_int, i64, i64, dbl,
@@ -63,7 +74,7 @@ def load(mutant: int = 0):
                                         ptr, i64, ptr]
         lib.rbd_oracle_reconstruct.restype = ctypes.c_int
         lib.rbd_oracle_reconstruct.argtypes = [ptr, i64, i64, i64, ptr, i64, i64, ptr, i64]
-        _libs[mutant] = lib
+        _libs[key] = lib
         return lib
 
 
@@ -79,11 +90,16 @@ def _p(a: np.ndarray):
 
 
 def compress(X, tol: float, d_max: int, start: int = 0, mode: str = "maxcol_abs",
-             rank_floor: float = RANK_FLOOR, mutant: int = 0, weights=None) -> dict:
+             rank_floor: float = RANK_FLOOR, mutant: int = 0, weights=None, threads: int = 0) -> dict:
     """Run Algorithm 1 on column-major FP64 X (m x n).  Returns a dict with Y (m x d),
     T (d x n), pivots, err, nu, fro (length d), next_pivot and d.  With `weights` (m positive
-    values, A = diag(weights)) the error of steps 2.2-2.4 is the A-norm (Section 3.2)."""
-    lib = load(mutant)
+    values, A = diag(weights)) the error of steps 2.2-2.4 is the A-norm (Section 3.2).
+    threads > 0 runs the OpenMP build on that many threads (the same results)."""
+    if threads > 0:
+        lib = load(omp=True)
+        lib.rbd_oracle_set_threads(int(threads))
+    else:
+        lib = load(mutant)
     X = _f64_colmajor(X)
     m, n = X.shape
     w = None

@@ -90,6 +90,16 @@ static double norm_a(const double* a, const double* w, int64_t m) {
 
 int rbd_oracle_version(void) { return 1; }
 
+#ifdef _OPENMP
+#include <omp.h>
+/* The OpenMP build (the all-core CPU baseline): threads for the column loops of Algorithm 1. */
+void rbd_oracle_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int rbd_oracle_threads(void) { return omp_get_max_threads(); }
+#else
+void rbd_oracle_set_threads(int n) { (void)n; }
+int rbd_oracle_threads(void) { return 1; }
+#endif
+
 /*
  * Algorithm 1.  X is m x n column-major (leading dimension ldx).  Outputs, with capacity d_max:
  *   Y       m x d_max, column-major (ldy): Y(:, k) = xi_k
@@ -117,9 +127,11 @@ static int compress_core(const double* X, int64_t m, int64_t n, int64_t ldx, con
 
     double* R = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n);
     double* v = (double*)malloc(sizeof(double) * (size_t)m);
-    if (!R || !v) {
+    double* ecol = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!R || !v || !ecol) {
         free(R);
         free(v);
+        free(ecol);
         return ORC_ENOMEM;
     }
 
@@ -131,6 +143,7 @@ static int compress_core(const double* X, int64_t m, int64_t n, int64_t ldx, con
             if (!isfinite(xj[r])) {
                 free(R);
                 free(v);
+                free(ecol);
                 return ORC_ENONFINITE;
             }
             R[j * m + r] = xj[r];
@@ -166,18 +179,25 @@ static int compress_core(const double* X, int64_t m, int64_t n, int64_t ldx, con
         if (vna < eps_r || vn <= rank_floor * xin) break;
         double* xi = Y + d * ldy;
         for (int64_t r = 0; r < m; ++r) xi[r] = (RBD_ORACLE_MUTANT == 6) ? v[r] : v[r] / vn;
-        /* T(d, :) = xi_d' X */
+        /* T(d, :) = xi_d' X (columns are independent; an OpenMP build gives each to one thread) */
+#pragma omp parallel for schedule(static)
         for (int64_t j = 0; j < n; ++j)
             T[j * ldt + d] = dot((RBD_ORACLE_MUTANT == 7) ? v : xi, X + j * ldx, m);
-        /* step 2.3: explicit residual, its column norms, max and argmax (lowest index) */
-        double ecur = -1.0, fro2 = 0.0;
-        int64_t inext = 0;
+        /* step 2.3: explicit residual and its column norms (independent columns), then their sum,
+           max and argmax (lowest index) in column order */
+#pragma omp parallel for schedule(static)
         for (int64_t j = 0; j < n; ++j) {
             double c = T[j * ldt + d];
             double* rj = R + j * m;
             for (int64_t r = 0; r < m; ++r) rj[r] -= c * xi[r];
             double ej = (RBD_ORACLE_MUTANT == 14) ? norm2(rj, m) : norm_a(rj, w, m);
             if (RBD_ORACLE_MUTANT == 5) ej = ej * ej;
+            ecol[j] = ej;
+        }
+        double ecur = -1.0, fro2 = 0.0;
+        int64_t inext = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            double ej = ecol[j];
             fro2 += ej * ej;
             int better = (RBD_ORACLE_MUTANT == 3) ? (ej >= ecur) : (ej > ecur);
             if (better) {
@@ -203,6 +223,7 @@ static int compress_core(const double* X, int64_t m, int64_t n, int64_t ldx, con
     *next_pivot = i;
     free(R);
     free(v);
+    free(ecol);
     return ORC_OK;
 }
 
