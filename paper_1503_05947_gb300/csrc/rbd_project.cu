@@ -53,10 +53,10 @@ __global__ void __launch_bounds__(256) project_kernel(ProjParams p, int64_t rows
                 if (c0 + col < p.k) v = load_v(p.V, p.vt, (c0 + col) * p.ldv + r);
             }
             float a, b;
-            split_double(y, a, b);
+            split_f64_fast(y, a, b);  // integer splits (FP64 arithmetic is slow on this part)
             yh[row][col] = a;
             yl[row][col] = b;
-            split_double(v, a, b);
+            split_f64_fast(v, a, b);
             vh[row][col] = a;
             vl[row][col] = b;
         }
@@ -162,11 +162,12 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(ReconParams p) {
             double y = 0.0, t = 0.0;
             if (r0 + a < p.m && l0 + b < p.d) y = p.Y[(l0 + b) * p.ldy + r0 + a];
             if (l0 + a < p.d && j0 + b < p.n) t = p.T[(j0 + b) * p.ldt + l0 + a];
+            // integer splits: FP64 arithmetic here would cost as much as the products below
             float hi, lo;
-            split_double(y, hi, lo);
+            split_f64_fast(y, hi, lo);
             yh[b][a] = hi;
             yl[b][a] = lo;
-            split_double(t, hi, lo);
+            split_f64_fast(t, hi, lo);
             th[b][a] = hi;
             tl[b][a] = lo;
         }
