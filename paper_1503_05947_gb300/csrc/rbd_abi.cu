@@ -66,7 +66,8 @@ bool plan_work(Work& w, int64_t m, int64_t n, int64_t ldx, int64_t d_max, int xt
     // The persistent loop kernel: one CTA per SM at most, each owning a block of R rows of Y.
     w.use_loop = 0;
     if (loop_max_smem > 0) {
-        const int64_t gl = std::min<int64_t>(num_sms, std::max<int64_t>(w.W, ceil_div(w.ldp, kLoopMaxRows)));
+        const int64_t gl = std::min<int64_t>(std::min<int64_t>(num_sms, kLoopMaxCtas),
+                                             std::max<int64_t>(w.W, ceil_div(w.ldp, kLoopMaxRows)));
         const int64_t R = round_up(ceil_div(w.ldp, gl), 4);
         if (R <= kLoopMaxRows) {
             const int64_t RS = (R % 8 == 4) ? R : R + 4;

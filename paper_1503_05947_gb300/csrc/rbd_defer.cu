@@ -62,6 +62,7 @@ struct DeferParams {
     Ctl* ctl;
     uint32_t* bar;        // grid barrier word (monotonic arrivals, abort bit)
     uint32_t* hcnt;       // shares of h published (monotonic, G per basis)
+    uint32_t* hdone;      // CTAs whose partial Y' v1 and ||v1||^2 are published (monotonic, G per basis)
     double* e;
     const double* xn2;
     float* ysb;           // [G][2][d_max][RS] split Y, row-block-major
@@ -400,9 +401,24 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
             }
             named_bar(1, NCONS);         // v1 and xi_{k-1} complete in shared memory
 
+            // The split v1 tiles of the pass (tile t holds [hi(rows_t) | lo(rows_t)] at t * 2 * MT)
+            // are all the pass needs from this CTA: they are published with the arrival at grid
+            // barrier 1, and O1' runs while the other CTAs arrive.
+            for (int r = tid; r < Rb; r += NCONS) {
+                const int64_t row = r0 + r;
+                const int64_t t = row / MT;
+                const int64_t rt = min((int64_t)MT, p.ldp - t * MT);
+                const int64_t off = t * 2 * MT + (row - t * MT);
+                p.vs[off] = v1h[r];
+                p.vs[off + rt] = v1l[r];
+            }
+            named_bar(1, NCONS);
+            if (tid == 0) grid_arrive(p.bar);  // barrier 1: arrival
+
             // ---------------- O1': hpart[b] = Y_b(:, 0:k)' v1 ----------------
-            // One thread per (column, row segment) of a chunk, four float-float chains over quads
-            // of rows, the segments combined in order through shared memory.
+            // A streamed slice (too long to stay in the ring) goes chunk by chunk: one thread per
+            // (column, row segment) of a chunk, four float-float chains over quads of rows, the
+            // segments combined in order through shared memory.
             // Columns lc, lc + 1 of the last call (nx = 2, or 1 without a deferred column) are the new
             // column xi_{k-1} and v1 itself, both from shared memory: its hpart entry and this block's
             // ||v1||^2 come out of the same pass over the chunk's rows.
@@ -451,12 +467,67 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 }
             };
             const int nx = deferred ? 2 : 1;
-            if (nch == 0) {
-                dots_chunk(nullptr, nullptr, 0, 0, nx);
-            } else if (resident) {
-                for (int64_t u = 0; u < nch; ++u) {
-                    const float* yh = stages + (size_t)(u % NB) * ybuf;
-                    dots_chunk(yh, yh + yplane, u * LC, (int)min((int64_t)LC, ncol - u * LC), (u == nch - 1) ? nx : 0);
+            if (resident) {
+                // Every column of the resident slice at once (column l < ncol in buffer l / LC, row
+                // offset (l % LC) RS), then xi_{k-1} and v1: one thread per (column, row segment),
+                // four float-float chains over quads of rows; segments only while the columns leave
+                // threads idle, their partial sums combined in order through shared memory.
+                const int lt = (int)ncol + nx;
+                const int nseg = (2 * lt >= NCONS) ? 1 : max(1, min(8, NCONS / lt));
+                const int sq = (NQ + nseg - 1) / nseg;
+                float* pf = reinterpret_cast<float*>(part) + ((dcount++ & 1u) ? 2 * NCONS : 0);
+                const int nh = (int)ncol + (deferred ? 1 : 0);  // columns with an hpart entry
+                auto publish = [&](int l, float s0, float c0) {
+                    const float2 r2 = make_float2(s0, c0);
+                    if (l < nh)
+                        reinterpret_cast<float2*>(p.hpart)[b * p.d_max + l] = r2;  // xi_{k-1}: index k - 1
+                    else
+                        reinterpret_cast<float2*>(p.nu2part)[b] = r2;
+                };
+                for (int task = tid; task < nseg * lt; task += NCONS) {
+                    const int l = task % lt, sg = task / lt;
+                    const float* ch;
+                    const float* cl;
+                    if (l < ncol) {
+                        const int u = l / LC;
+                        ch = stages + (size_t)u * ybuf + (size_t)(l - u * LC) * RS;
+                        cl = ch + yplane;
+                    } else {
+                        const bool vcol = l > ncol || !deferred;
+                        ch = vcol ? v1h : xih;
+                        cl = vcol ? v1l : xil;
+                    }
+                    const int q0 = sg * sq, q1 = min(NQ, q0 + sq);
+                    float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (ok)
+                        for (int qq = q0; qq < q1; ++qq) {
+                            const float4 a = *reinterpret_cast<const float4*>(ch + 4 * qq);
+                            const float4 al = *reinterpret_cast<const float4*>(cl + 4 * qq);
+                            const float4 v = *reinterpret_cast<const float4*>(v1h + 4 * qq);
+                            const float4 vl = *reinterpret_cast<const float4*>(v1l + 4 * qq);
+                            ff_mac2(s4[0], c4[0], a.x, al.x, v.x, vl.x);
+                            ff_mac2(s4[1], c4[1], a.y, al.y, v.y, vl.y);
+                            ff_mac2(s4[2], c4[2], a.z, al.z, v.z, vl.z);
+                            ff_mac2(s4[3], c4[3], a.w, al.w, v.w, vl.w);
+                        }
+                    ff_add_acc(s4[0], c4[0], s4[1], c4[1]);
+                    ff_add_acc(s4[2], c4[2], s4[3], c4[3]);
+                    ff_add_acc(s4[0], c4[0], s4[2], c4[2]);
+                    if (nseg == 1) {
+                        publish(l, s4[0], c4[0]);
+                    } else {
+                        pf[2 * (sg * lt + l)] = s4[0];
+                        pf[2 * (sg * lt + l) + 1] = c4[0];
+                    }
+                }
+                if (nseg > 1) {
+                    named_bar(1, NCONS);
+                    if (tid < lt) {
+                        float s0 = pf[2 * tid], c0 = pf[2 * tid + 1];
+                        for (int sg = 1; sg < nseg; ++sg)
+                            ff_add_acc(s0, c0, pf[2 * (sg * lt + tid)], pf[2 * (sg * lt + tid) + 1]);
+                        publish(tid, s0, c0);
+                    }
                 }
             } else {
                 for (int64_t u = nch; u < 2 * nch; ++u) {
@@ -468,16 +539,9 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     if (u + NB < ytot) y_issue(u + NB, ncol, nch);  // dots_chunk's barrier freed it
                 }
             }
-            // the split v1 tiles of the pass: tile t holds [hi(rows_t) | lo(rows_t)] at t * 2 * MT
-            for (int r = tid; r < Rb; r += NCONS) {
-                const int64_t row = r0 + r;
-                const int64_t t = row / MT;
-                const int64_t rt = min((int64_t)MT, p.ldp - t * MT);
-                const int64_t off = t * 2 * MT + (row - t * MT);
-                p.vs[off] = v1h[r];
-                p.vs[off + rt] = v1l[r];
-            }
-            named_bar_arrive(3, NCONS + 32);  // every consumer is done with the ring
+            // this CTA's partial Y' v1 and ||v1||^2 are published
+            named_bar(1, NCONS);
+            if (tid == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p.hdone) : "memory");
         } else if (warp == PROD) {
             named_bar(2, NCONS + 32);
             if (lane == 0 && run_pass) {
@@ -494,15 +558,24 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     }
                 }
             }
-            named_bar(3, NCONS + 32);
+            // barrier 1: this lane waits for the other CTAs' arrivals while the consumers run O1'
+            if (lane == 0) sfl[0] = grid_poll(p.bar, (uint32_t)G * (gen + 1u), ctl, p.wait_ns);
         }
-        if (!grid_sync(p.bar, (uint32_t)G, gen, &sfl[0], ctl, p.wait_ns)) break;  // barrier 1 (uniform result)
+        // barrier 1 passed (uniform result), and every consumer is done with the ring
+        __syncthreads();
+        ++gen;
+        if (!sfl[0]) break;
 
         int32_t dec = STOP_NONE;
         if (warp == SVC) {
             // ---------------- second sweep over the grid: h, nu, the stop tests ----------------
             double nu2 = 0.0, fs = 0.0, hh = 0.0;
             const double xn2p = (lane == 0) ? __ldg(&p.xn2[piv]) : 0.0;  // loads of this round first
+            // every CTA's partial Y' v1 and ||v1||^2 (published after its arrival at barrier 1)
+            if (!wait_counter(p.hdone, p.bar, (uint32_t)G * (uint32_t)(k - p.k0 + 1), p.wait_ns)) {
+                if (lane == 0) loop_abort(ctl, p.bar, ST_ETIMEOUT);
+                ok = false;
+            }
 #pragma unroll 4
             for (int64_t bb = lane; bb < G; bb += 32) {
                 const float2 nv = __ldcg(reinterpret_cast<const float2*>(p.nu2part) + bb);
@@ -815,9 +888,17 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                         if (fin_here) {
                             __threadfence();
                             if (colv) {
+                                // the shares in CTA order, four loads in flight at a time
                                 double acc = 0.0;
-                                for (uint32_t sl = 0; sl < ncontrib; ++sl)
-                                    acc += __ldcg(&p.gslot[(g * p.KMAX + sl) * C + cwl]);
+                                for (uint32_t s0 = 0; s0 < ncontrib; s0 += 4) {
+                                    double sv[4];
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q)
+                                        sv[q] = (s0 + q < ncontrib) ? __ldcg(&p.gslot[(g * p.KMAX + s0 + q) * C + cwl]) : 0.0;
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q)
+                                        if (s0 + q < ncontrib) acc += sv[q];
+                                }
                                 tot = acc;
                             }
                             if (tid == 0) p.gcnt[g] = 0;
@@ -971,17 +1052,25 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
         // ---------------- A: argmax over CTAs ----------------
         if (warp == 0) {
             // keys compared as integers: e_j >= 0, whose FP64 bit patterns order like the values
+            // every candidate load in flight before the comparisons: in a loop whose trip count the
+            // compiler cannot see, each round trip to L2 would wait for the one before
+            constexpr int SL = kLoopMaxCtas / 32;
+            long long ckv[SL];
+            int64_t cjv[SL];
+#pragma unroll
+            for (int i = 0; i < SL; ++i) {
+                const int64_t cb = lane + 32 * i;
+                ckv[i] = (cb < G) ? __ldcg(reinterpret_cast<const long long*>(&p.pbest_e[cb])) : LLONG_MIN;
+                cjv[i] = (cb < G) ? __ldcg(reinterpret_cast<const long long*>(&p.pbest_j[cb])) : INT64_MAX;
+            }
             long long bk = LLONG_MIN;
             int64_t bj = INT64_MAX;
-#pragma unroll 8
-            for (int64_t cb = lane; cb < G; cb += 32) {
-                const long long ck = __ldcg(reinterpret_cast<const long long*>(&p.pbest_e[cb]));
-                const int64_t cj = __ldcg(reinterpret_cast<const long long*>(&p.pbest_j[cb]));
-                if (better_key(ck, cj, bk, bj)) {
-                    bk = ck;
-                    bj = cj;
+#pragma unroll
+            for (int i = 0; i < SL; ++i)
+                if (better_key(ckv[i], cjv[i], bk, bj)) {
+                    bk = ckv[i];
+                    bj = cjv[i];
                 }
-            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const long long ok2 = __shfl_down_sync(0xffffffffu, bk, o);
@@ -1086,6 +1175,7 @@ cudaError_t launch_defer(const Work& w, const void* X, double* Y, int64_t ldy, d
     p.ctl = w.ctl;
     p.bar = &w.ctl->bar[0];
     p.hcnt = &w.ctl->bar[1];
+    p.hdone = &w.ctl->bar[2];
     p.e = w.e;
     p.xn2 = w.xn2;
     p.ysb = w.ysb;

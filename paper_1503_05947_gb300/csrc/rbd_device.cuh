@@ -66,7 +66,9 @@ struct Ctl {
     int32_t mode;         // MODE_*
     int32_t pad1;
     int64_t d_max;
-    uint32_t bar[2];      // grid barrier of the persistent loop kernel: {arrivals (monotonic), unused}
+    uint32_t bar[4];      // counters of the persistent loop kernels (monotonic within a launch):
+                          // {grid-barrier arrivals, shares of h summed, partial dot products
+                          // published, unused}
 };
 
 // Element idx of X stored as FP64 (xt 0), FP32 (1) or BF16 (2), widened exactly to FP64.

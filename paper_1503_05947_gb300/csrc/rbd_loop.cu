@@ -539,9 +539,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             if (warp < NW) {
                 const int64_t lb0 = (k * b) / G, lb1 = (k * (b + 1)) / G;
                 for (int64_t l = lb0 + warp; l < lb1; l += NW) {
-                    double acc = 0.0;
-                    #pragma unroll 8
-                    for (int64_t bb = lane; bb < G; bb += 32) acc += __ldcg(&p.hpart[bb * p.d_max + l]);
+                    double acc = lane_sum_ctas(p.hpart + l, p.d_max, G, lane);
                     acc = warp_sum_double(acc);
                     if (lane == 0) p.h[l] = acc;
                 }
@@ -595,12 +593,8 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
             // independent loads first, so that their round trips overlap
             const double xn2p = (lane == 0) ? __ldg(&p.xn2[piv]) : 0.0;
             const double frol = (lane == 0 && k > 0 && mode == MODE_FRO_REL) ? __ldcg(&ctl->fro_last) : 0.0;
-            double acc = 0.0, acc2 = 0.0;
-            #pragma unroll 8
-            for (int64_t bb = lane; bb < G; bb += 32) {
-                acc += __ldcg(&p.nu2part[bb]);
-                if constexpr (WT) acc2 += __ldcg(&p.nu2part[G + bb]);
-            }
+            double acc = lane_sum_ctas(p.nu2part, 1, G, lane), acc2 = 0.0;
+            if constexpr (WT) acc2 = lane_sum_ctas(p.nu2part + G, 1, G, lane);
             acc = warp_sum_double(acc);
             if constexpr (WT) acc2 = warp_sum_double(acc2);
             if (lane == 0) {
@@ -646,9 +640,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
                 if (warp < NW) {
                     const int64_t lb0 = (k * b) / G, lb1 = (k * (b + 1)) / G;
                     for (int64_t l = lb0 + warp; l < lb1; l += NW) {
-                        double acc = 0.0;
-                        #pragma unroll 8
-                        for (int64_t bb = lane; bb < G; bb += 32) acc += __ldcg(&p.hpart[bb * p.d_max + l]);
+                        double acc = lane_sum_ctas(p.hpart + l, p.d_max, G, lane);
                         acc = warp_sum_double(acc);
                         if (lane == 0) p.h[l] = acc;
                     }
@@ -855,17 +847,24 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS, 1) loop_kernel(LoopParam
 
         // ---------------- A: argmax over CTAs, Frobenius residual ----------------
         if (warp == 0) {
+            // every candidate load in flight before the comparisons
+            constexpr int SL = kLoopMaxCtas / 32;
+            double cev[SL];
+            int64_t cjv[SL];
+#pragma unroll
+            for (int i = 0; i < SL; ++i) {
+                const int64_t cb = lane + 32 * i;
+                cev[i] = (cb < G) ? __ldcg(&p.pbest_e[cb]) : -1.0;
+                cjv[i] = (cb < G) ? __ldcg(reinterpret_cast<const long long*>(&p.pbest_j[cb])) : INT64_MAX;
+            }
             double be = -1.0;
             int64_t bj = INT64_MAX;
-            #pragma unroll 8
-            for (int64_t cb = lane; cb < G; cb += 32) {
-                const double ce = __ldcg(&p.pbest_e[cb]);
-                const int64_t cj = __ldcg(reinterpret_cast<const long long*>(&p.pbest_j[cb]));
-                if (better(ce, cj, be, bj)) {
-                    be = ce;
-                    bj = cj;
+#pragma unroll
+            for (int i = 0; i < SL; ++i)
+                if (better(cev[i], cjv[i], be, bj)) {
+                    be = cev[i];
+                    bj = cjv[i];
                 }
-            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const double oe = __shfl_down_sync(0xffffffffu, be, o);

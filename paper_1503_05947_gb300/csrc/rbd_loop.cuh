@@ -5,6 +5,7 @@
 #pragma once
 
 #include "rbd_device.cuh"
+#include "rbd_work.h"
 
 namespace rbd {
 
@@ -47,6 +48,25 @@ __device__ __forceinline__ void loop_abort(Ctl* ctl, uint32_t* bar, int32_t st) 
     atomicOr(bar, kAbortBit);
 }
 
+// Thread 0's wait for a grid barrier: its arrival counter reaching target.  1 when passed, 0 when
+// the abort bit appeared or limit_ns elapsed (the latter raises the abort).
+__device__ __forceinline__ int grid_poll(uint32_t* bar, uint32_t target, Ctl* ctl, uint64_t limit_ns) {
+    uint32_t v = ld_acquire_u32(bar);
+    if (!(v & kAbortBit) && v < target) {
+        const uint64_t t0 = globaltimer_ns();
+        while (true) {
+            v = ld_acquire_u32(bar);
+            if ((v & kAbortBit) || v >= target) break;
+            if (globaltimer_ns() - t0 > limit_ns) {
+                loop_abort(ctl, bar, ST_ETIMEOUT);
+                v = kAbortBit;
+                break;
+            }
+        }
+    }
+    return (v & kAbortBit) ? 0 : 1;
+}
+
 // Grid-wide barrier for a cooperative launch; called by every thread of every CTA.  The arrival
 // counter only grows: the barrier with index gen (1, 2, ...) is passed once it reaches
 // nblocks * gen, so no CTA has to reset it and the last arrival needs no extra release step.
@@ -55,30 +75,38 @@ __device__ __forceinline__ void loop_abort(Ctl* ctl, uint32_t* bar, int32_t st) 
 __device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, uint32_t& gen, int* s_ok, Ctl* ctl,
                                           uint64_t limit_ns = kBarrierLimitNs) {
     __syncthreads();
+    ++gen;  // in every thread: any thread may poll the next barrier
     if (threadIdx.x == 0) {
-        int ok = 1;
-        const uint32_t target = nblocks * (++gen);
         // arrival without a returned value (no round trip before the first poll); the first poll
         // of the same word already sees it
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
-        uint32_t v = ld_acquire_u32(bar);
-        if (!(v & kAbortBit) && v < target) {
-            const uint64_t t0 = globaltimer_ns();
-            while (true) {
-                v = ld_acquire_u32(bar);
-                if ((v & kAbortBit) || v >= target) break;
-                if (globaltimer_ns() - t0 > limit_ns) {
-                    loop_abort(ctl, bar, ST_ETIMEOUT);
-                    v = kAbortBit;
-                    break;
-                }
-            }
-        }
-        if (v & kAbortBit) ok = 0;
-        *s_ok = ok;
+        *s_ok = grid_poll(bar, nblocks * gen, ctl, limit_ns);
     }
     __syncthreads();
     return *s_ok != 0;
+}
+
+// One lane's share of a sum over the CTAs: v[b * stride] for b = lane, lane + 32, ... (< G),
+// added in that order.  Every load is issued before the first addition: in a loop whose trip
+// count the compiler cannot see, each round trip to L2 would wait for the one before.
+__device__ __forceinline__ double lane_sum_ctas(const double* v, int64_t stride, int64_t G, int lane) {
+    constexpr int SL = kLoopMaxCtas / 32;
+    double x[SL];
+#pragma unroll
+    for (int i = 0; i < SL; ++i) x[i] = (lane + 32 * i < G) ? __ldcg(v + (int64_t)(lane + 32 * i) * stride) : 0.0;
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < SL; ++i)
+        if (lane + 32 * i < G) acc += x[i];
+    return acc;
+}
+
+// The arrival half of grid_sync, so that a CTA can work between publishing its writes and waiting
+// for everyone else's: ONE thread, after a barrier among the threads whose writes it publishes (the
+// release is cumulative over them).  The wait is grid_poll (target nblocks * gen, gen counted in
+// every thread) followed by a CTA barrier that broadcasts its result.
+__device__ __forceinline__ void grid_arrive(uint32_t* bar) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
 }
 
 }  // namespace rbd

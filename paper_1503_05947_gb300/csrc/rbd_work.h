@@ -132,6 +132,7 @@ struct TileCfgW : TileCfg<XT> {
 constexpr int kGemvRows = 128;     // rows per CTA of the row-parallel GEMVs
 constexpr int kGemvTargetCtas = 304;
 constexpr int kLoopMaxRows = 512;  // largest row block per CTA of the persistent loop kernel
+constexpr int kLoopMaxCtas = 256;  // most CTAs of a persistent loop kernel (8 per lane of a warp)
 
 struct Work {
     // sizes
