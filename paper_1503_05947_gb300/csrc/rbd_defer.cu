@@ -104,7 +104,7 @@ __host__ __device__ inline DeferSmem defer_smem_layout(int R, int KC) {
     s.coef = o;
     o += (size_t)4 * KC * 4;                       // [h hi | h lo | t hi | t lo]
     s.tfb = o;
-    // T(0:k, group) in FP32 during the pass; the row-sum partials of F (4 NCONS doubles) before it
+    // T(0:k, group) in FP32 during the pass; the row-sum partials of F (4 NCONS float pairs) before it
     const size_t tfb_bytes = (size_t)KC * Cfg::C * 4, fp_bytes = (size_t)4 * NCONS * 8;
     o += (tfb_bytes > fp_bytes) ? tfb_bytes : fp_bytes;
     s.corr = o;
@@ -374,15 +374,18 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 v1s[r] = v;
                 split_f64_fast(v, v1h[r], v1l[r]);
             };
-            // the segments' partial sums of each row, added in FP64 in segment order (v1 = x - Y t
-            // cancels heavily when the pivot nearly lies in span(Y))
-            double* fpart = reinterpret_cast<double*>(tfb);  // [sg][pr][B0, B1, A0, A1]
+            // The segments' partial sums of each row, added in segment order without loss: the high
+            // parts through a chain of exact TwoSums, their rounding errors and the low parts into a
+            // float-float accumulator some 2^-24 the size of the sum, so that the one rounding left
+            // is the final conversion to FP64 (v1 = x - Y t cancels heavily when the pivot nearly
+            // lies in span(Y); FP64 instructions are slow on this part).
+            float2* fpart = reinterpret_cast<float2*>(tfb);  // [sg][pr][B0, B1, A0, A1]
             if (active) {
-                double* o = fpart + ((size_t)sg * NPR + pr) * 4;
-                o[0] = ff_to_double(b0s, b0c);
-                o[1] = ff_to_double(b1s, b1c);
-                o[2] = (amode == 1) ? (double)a0s : ff_to_double(a0s, a0c);
-                o[3] = (amode == 1) ? (double)a1s : ff_to_double(a1s, a1c);
+                float2* o = fpart + ((size_t)sg * NPR + pr) * 4;
+                o[0] = make_float2(b0s, b0c);
+                o[1] = make_float2(b1s, b1c);
+                o[2] = make_float2(a0s, (amode == 1) ? 0.f : a0c);
+                o[3] = make_float2(a1s, (amode == 1) ? 0.f : a1c);
             }
             named_bar(1, NCONS);
 #pragma unroll
@@ -391,11 +394,21 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                 if (r >= R) break;
                 double A = 0.0, B = 0.0;
                 if (r < Rb && ncol > 0) {
-                    const double* pin = fpart + (size_t)(r >> 1) * 4 + (r & 1);
-                    for (int sgi = 0; sgi < NSG; ++sgi) {
-                        B += pin[(size_t)sgi * NPR * 4];
-                        A += pin[(size_t)sgi * NPR * 4 + 2];
+                    const float2* pin = fpart + (size_t)(r >> 1) * 4 + (r & 1);
+                    float bs = pin[0].x, beh = pin[0].y, bel = 0.f;
+                    float as = pin[2].x, aeh = pin[2].y, ael = 0.f;
+                    for (int sgi = 1; sgi < NSG; ++sgi) {
+                        const float2 pb = pin[(size_t)sgi * NPR * 4], pa = pin[(size_t)sgi * NPR * 4 + 2];
+                        float e;
+                        two_sum(bs, pb.x, bs, e);
+                        ff_add(beh, bel, e, 0.f);
+                        ff_add(beh, bel, pb.y, 0.f);
+                        two_sum(as, pa.x, as, e);
+                        ff_add(aeh, ael, e, 0.f);
+                        ff_add(aeh, ael, pa.y, 0.f);
                     }
+                    B = (double)bs + ((double)beh + (double)bel);
+                    A = (double)as + ((double)aeh + (double)ael);
                 }
                 fin(r, i, A, B);
             }
@@ -676,7 +689,7 @@ __global__ void __launch_bounds__(TileCfg<XT>::THREADS + 32, 1) defer_kernel(Def
                     // prefetched into L2 during the orthogonalisation (issuing them into the ring
                     // before barrier 1 would load the memory system the barrier's atomics cross).
                     for (int64_t i = 0; i < nunits; ++i) {
-                        if (mbar_try_wait(svcb, spar) && vfl[1] != STOP_NONE) {
+                        if (mbar_test_wait(svcb, spar) && vfl[1] != STOP_NONE) {
                             issued = i;  // the basis was rejected: stop streaming
                             break;
                         }
