@@ -628,7 +628,9 @@ BATCH_WORKLOAD = ("2048 FP32 matrices U diag(s) V' (Haar U, V; s_i = exp(-r i), 
 
 def batched_forms(dev) -> dict:
     """The batched form: the 2048-matrix workload compressed by one persistent launch captured in a
-    CUDA graph (pipeline depth chosen by the plan's autotuner), against the single-matrix path
+    CUDA graph, with the default launch shape and with the one the plan's autotuner picks (column
+    group width, tile rows, team sizing, ring depth; the tuning time is reported), against the
+    single-matrix path
     (rbd_compress per matrix, FP32 and FP64 copies) timed on a seeded sample of 64 matrices and
     scaled to the whole batch by sum((d + 1) m n)."""
     import torch
@@ -643,27 +645,35 @@ def batched_forms(dev) -> dict:
         items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"],
                           "d_hint": sp["d_hint"]})
     plan = rbd.BatchPlan(items)
-    stages = plan.tune()
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(torch.cuda.current_stream(dev))
-    with torch.cuda.stream(side):
-        plan.run()
-    torch.cuda.current_stream(dev).wait_stream(side)
-    torch.cuda.synchronize(dev)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        plan.run()
-    graph.replay()
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    reps = 3
-    e0.record()
-    for _ in range(reps):
+
+    def graph_ms(reps=3):
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            plan.run()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            plan.run()
         graph.replay()
-    e1.record()
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / reps
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    untuned = plan.config()
+    ms_untuned = graph_ms()
+    import tempfile
+    t0 = time.perf_counter()
+    tuned = plan.tune(cache=os.path.join(tempfile.mkdtemp(), "batch_tune.json"))  # a fresh tuning
+    tune_s = time.perf_counter() - t0
+    ms = graph_ms()
     res = plan.results()
     cost = [(r["d"] + 1) * it["X"].shape[0] * it["X"].shape[1] for r, it in zip(res, items)]
     xbytes = 4.0 * sum(cost)
@@ -684,13 +694,16 @@ def batched_forms(dev) -> dict:
 
     s32 = single(torch.float32)
     s64 = single(torch.float64)
-    out = {"workload": BATCH_WORKLOAD, "matrices": len(items), "stages": stages, "graph": True, "ms": ms,
+    out = {"workload": BATCH_WORKLOAD, "matrices": len(items), "graph": True,
+           "launch_shape_default": untuned, "ms_default": ms_untuned,
+           "launch_shape_tuned": {k: tuned[k] for k in ("cols", "tile_rows", "team_pct", "stages")},
+           "tune_s": tune_s, "bucket": plan.bucket(), "speedup_tuned_vs_default": ms_untuned / ms, "ms": ms,
            "bases_total": int(sum(r["d"] for r in res)), "x_bytes_streamed": xbytes, "gbs": xbytes / (ms * 1e-3) / 1e9,
            "single_matrix_f32_ms_est": s32, "speedup_vs_single_f32": s32 / ms,
            "single_matrix_f64_ms_est": s64, "speedup_vs_single_f64": s64 / ms,
            "single_sample": "64 seeded matrices compressed one by one (rbd_compress, synchronous calls), "
                             "scaled by sum((d + 1) m n)"}
-    del plan, items, graph
+    del plan, items
     torch.cuda.empty_cache()
     return out
 

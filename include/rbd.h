@@ -312,7 +312,8 @@ rbd_status rbd_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy,
  * persistent launch.  The plan orders the matrices by estimated work (m n d, with d the hint or
  * d_max) and gives the largest a team of up to 16 CTAs; each CTA takes the next member slot from
  * the queue and runs that matrix's greedy loop with its team to the end.  Results match
- * rbd_compress on each matrix and do not depend on the team sizes.
+ * rbd_compress on each matrix to its accuracy; the plan's launch shape (rbd_batch_config) changes
+ * them by rounding only.
  *
  * Limits: every matrix has m <= 4096 rows and d_max <= 512 (larger matrices: rbd_compress);
  * storage type RBD_F64 or RBD_F32, the same for the whole batch.
@@ -367,12 +368,34 @@ rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst,
    CUDA graph and replayed.  results: device array of `count` rbd_batch_result. */
 rbd_status rbd_batch_run(rbd_batch_plan plan, rbd_batch_result* results, void* stream);
 
-/* Autotuner: time the run with each candidate pipeline depth (ring stages of the fused pass and
-   of the Gram-Schmidt streams) on this batch and keep the fastest in the plan.  Synchronises
-   `stream`; the outputs hold the results of the last trial.  *stages_out (may be NULL) receives
-   the choice. */
+/* The launch shape of a batched run (one per plan; the tuner picks it per batch). */
+typedef struct rbd_batch_config {
+    int32_t cols;       /* columns per group of the fused pass: 16 or 32 (a CTA's 8 consumer warps
+                           take 2 or 4 columns each) */
+    int32_t tile_rows;  /* rows per tile of X streamed into a ring stage: 128 or 256 */
+    int32_t team_pct;   /* team sizing: a matrix gets ceil(team_pct / 100 * work / share) member
+                           CTAs (share = the batch's work per CTA), at most 16; 75, 150 or 300
+                           (default 150) */
+    int32_t stages;     /* ring stages of the pass, 2 ..  (128 KiB / stage bytes); 0 = the most */
+} rbd_batch_config;
+
+/* Autotuner: time the run of this batch under every launch shape (cols x tile_rows x team_pct,
+   each at its deepest ring), then the ring depths of the fastest, and keep the winner in the plan
+   (its workspace holds every candidate's layout: rbd_batch_workspace_bytes is the largest).  A
+   shape changes the results by rounding only: the tile rows not at all (each column's products
+   are summed over the same rows in the same order), the team size the grouping of the sums of h
+   and ||v2||^2 over row blocks, the group width that of the Frobenius sum over columns.  A plan
+   gives the same bits run after run (and under graph replay).  Synchronises `stream`; the outputs
+   hold the results of the last trial.  *chosen (may be NULL) receives the choice. */
 rbd_status rbd_batch_tune(rbd_batch_plan plan, rbd_batch_result* results, void* stream,
-                          int32_t* stages_out);
+                          rbd_batch_config* chosen);
+
+/* The plan's current launch shape, and a shape to apply without tuning (e.g. one cached from an
+   earlier tuning of a batch like this one).  set_config re-lays the workspace out and uploads the
+   descriptor table on `stream` (synchronised).  Errors: RBD_EINVAL for a shape outside the
+   values above. */
+rbd_status rbd_batch_plan_config(rbd_batch_plan plan, rbd_batch_config* cfg);
+rbd_status rbd_batch_plan_set_config(rbd_batch_plan plan, const rbd_batch_config* cfg, void* stream);
 
 rbd_status rbd_batch_plan_destroy(rbd_batch_plan plan);
 

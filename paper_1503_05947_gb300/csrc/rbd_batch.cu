@@ -38,12 +38,9 @@ namespace rbd {
 
 namespace {
 
-constexpr int kBC = 16;                      // columns per group
-constexpr int kBCPW = 2;                     // columns per consumer warp
-constexpr int kBNW = kBC / kBCPW;            // consumer warps
+constexpr int kBNW = 8;                      // consumer warps
 constexpr int kBNCONS = kBNW * 32;
 constexpr int kBThreads = kBNCONS + 32;      // + producer warp
-constexpr int kBMT = 256;                    // rows per tile
 constexpr int kBMaxRows = 4096;              // padded rows per matrix
 constexpr int kBMaxD = 512;
 constexpr int kBQR = kBMaxRows / kBNCONS;    // rows per consumer thread
@@ -51,10 +48,14 @@ constexpr int kBRingBytes = 128 * 1024;
 constexpr int kBMaxLC = 64;                  // Y columns per Gram-Schmidt chunk
 constexpr int kBNB = 2;                      // Y chunk buffers (the ring in halves)
 
-template <int P>
+// Launch shape of the fused pass: CPW columns per consumer warp (a column group of C = 8 CPW
+// columns) and MT rows per tile; both are chosen per plan (rbd_batch_config, the autotuner).
+template <int P, int CPW, int MT>
 struct BCfg {
-    static constexpr int STAGE_BYTES = kBC * P * kBMT * 4;
+    static constexpr int C = kBNW * CPW;
+    static constexpr int STAGE_BYTES = C * P * MT * 4;
     static constexpr int SMAX = kBRingBytes / STAGE_BYTES;
+    static_assert(MT % 128 == 0 && SMAX >= 2 && SMAX <= 32, "ring of 2..32 stages");
 };
 
 // Device descriptor of one matrix (built on the host, uploaded by plan_create).
@@ -97,6 +98,7 @@ struct BatchParams {
     int32_t* status;             // per matrix (zero before the run)
     rbd_batch_result* res;
     int S;                       // ring stages used by the pass (<= SMAX)
+    int C, MT;                   // the plan's column-group width and tile rows (initial pass)
     uint64_t wait_ns;            // bound on a ring or Y-chunk wait (the exit drain keeps kWaitLimitNs)
     uint64_t team_ns;            // bound on a team barrier
 };
@@ -132,15 +134,16 @@ __global__ void __launch_bounds__(256) batch_init_kernel(BatchParams bp) {
         double* Ie = Ig.e;
         double* Ixn2 = Ig.xn2;
         const int64_t j = q - bp.colstart[lo];
-        const int64_t g = j / kBC;
-        const int c = (int)(j % kBC);
+        const int64_t C = bp.C, MT = bp.MT;
+        const int64_t g = j / C;
+        const int c = (int)(j % C);
         const bool live = j < In;
         float s = 0.f, cc = 0.f;
         int bad = ST_OK;
         for (int64_t r0 = 4 * lane; r0 < Ildp; r0 += 128) {
-            const int64_t t = r0 / kBMT;
-            const int64_t rt = min((int64_t)kBMT, Ildp - t * kBMT);
-            const int64_t base = g * kBC * P * Ildp + t * kBC * P * kBMT + (int64_t)c * P * rt + (r0 - t * kBMT);
+            const int64_t t = r0 / MT;
+            const int64_t rt = min(MT, Ildp - t * MT);
+            const int64_t base = g * C * P * Ildp + t * C * P * MT + (int64_t)c * P * rt + (r0 - t * MT);
             float hv[4], lv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -185,9 +188,10 @@ __global__ void __launch_bounds__(256) batch_init_kernel(BatchParams bp) {
 }
 
 // ---------------------------------------------------------------- the per-matrix loop
-template <int P>
+template <int P, int CPW, int MT>
 __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
-    using Cfg = BCfg<P>;
+    using Cfg = BCfg<P, CPW, MT>;
+    constexpr int C = Cfg::C;
     constexpr int SMAX = Cfg::SMAX;
     constexpr int STAGE_F = Cfg::STAGE_BYTES / 4;
     extern __shared__ __align__(128) unsigned char bsm[];
@@ -536,10 +540,10 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                             ok = false;
                             break;
                         }
-                        const uint32_t rows = (uint32_t)min((int64_t)kBMT, ldp - t * kBMT);
-                        const uint32_t bytes = (uint32_t)(kBC * P) * rows * 4u;
+                        const uint32_t rows = (uint32_t)min((int64_t)MT, ldp - t * MT);
+                        const uint32_t bytes = (uint32_t)(C * P) * rows * 4u;
                         mbar_arrive_expect_tx(&full[ps], bytes);
-                        bulk_g2s(ring + (size_t)ps * STAGE_F, I.planes + g * kBC * P * ldp + t * kBC * P * kBMT, bytes,
+                        bulk_g2s(ring + (size_t)ps * STAGE_F, I.planes + g * C * P * ldp + t * C * P * MT, bytes,
                                  &full[ps], pol_x);
                         iss_mask |= 1u << ps;
                         iss_par = (iss_par & ~(1u << ps)) | (pph << ps);
@@ -555,13 +559,12 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     }
                 }
             } else {
-                float acc_s[kBCPW][4], acc_c[kBCPW][4];
+                float acc_s[CPW][4], acc_c[CPW][4];
 #pragma unroll
-                for (int qq = 0; qq < kBCPW; ++qq)
+                for (int qq = 0; qq < CPW; ++qq)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
-                // lanes 0 and 1 finalise one column each (their FP64 work runs side by side)
-                static_assert(kBCPW == 2, "two columns per consumer warp");
+                // lanes 0 .. CPW-1 finalise one column each (their FP64 work runs side by side)
                 double best_e = -1.0, esum = 0.0;
                 int64_t best_j = INT64_MAX;
                 double e_old = 0.0;
@@ -573,21 +576,21 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                         cs = 0;
                         cph ^= 1u;
                     }
-                    const int64_t c0 = g * kBC;
-                    const int ncols = (int)min((int64_t)kBC, n - c0);
-                    if (t == 0 && lane < kBCPW) {
-                        const int cw = warp * kBCPW + lane;
+                    const int64_t c0 = g * C;
+                    const int ncols = (int)min((int64_t)C, n - c0);
+                    if (t == 0 && lane < CPW) {
+                        const int cw = warp * CPW + lane;
                         e_old = (cw < ncols) ? __ldcg(&I.e[c0 + cw]) : 0.0;
                     }
                     if (ok && !mbar_wait(&full[s], ph, bp.wait_ns)) ok = false;
-                    const int rows = (int)min((int64_t)kBMT, ldp - t * kBMT);
+                    const int rows = (int)min((int64_t)MT, ldp - t * MT);
                     if (ok) {
                         const float* st = ring + (size_t)s * STAGE_F;
-                        if (rows == kBMT)
-                            consume_tile_xi<P, kBCPW, kBMT, true>(st, vh + t * kBMT, vl + t * kBMT, kBMT, warp, lane,
+                        if (rows == MT)
+                            consume_tile_xi<P, CPW, MT, true>(st, vh + t * MT, vl + t * MT, MT, warp, lane,
                                                                   acc_s, acc_c);
                         else
-                            consume_tile_xi<P, kBCPW, kBMT, false>(st, vh + t * kBMT, vl + t * kBMT, rows, warp, lane,
+                            consume_tile_xi<P, CPW, MT, false>(st, vh + t * MT, vl + t * MT, rows, warp, lane,
                                                                    acc_s, acc_c);
                     }
                     __syncwarp();
@@ -595,24 +598,28 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     if (++t < NT) continue;
                     t = 0;
                     // end of column group g: T(k, j), e_j, the running argmax
-                    float fsq[kBCPW], fcq[kBCPW];
+                    // each column's total (valid in lane 0), then lane qq takes column qq
+                    float my_s = 0.f, my_c = 0.f;
 #pragma unroll
-                    for (int qq = 0; qq < kBCPW; ++qq) {
+                    for (int qq = 0; qq < CPW; ++qq) {
                         float sq = acc_s[qq][0], cq = acc_c[qq][0];
 #pragma unroll
                         for (int e = 1; e < 4; ++e) ff_add(sq, cq, acc_s[qq][e], acc_c[qq][e]);
                         warp_sum_ff(sq, cq);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) acc_s[qq][e] = acc_c[qq][e] = 0.f;
-                        fsq[qq] = sq;
-                        fcq[qq] = cq;
+                        sq = __shfl_sync(0xffffffffu, sq, 0);
+                        cq = __shfl_sync(0xffffffffu, cq, 0);
+                        if (lane == qq) {
+                            my_s = sq;
+                            my_c = cq;
+                        }
                     }
-                    const float s1 = __shfl_sync(0xffffffffu, fsq[1], 0), c1 = __shfl_sync(0xffffffffu, fcq[1], 0);
-                    if (lane < kBCPW) {
-                        const int cw = warp * kBCPW + lane;
+                    if (lane < CPW) {
+                        const int cw = warp * CPW + lane;
                         if (cw < ncols) {
                             const int64_t j = c0 + cw;
-                            const double cj = (lane == 0) ? ff_to_double(fsq[0], fcq[0]) : ff_to_double(s1, c1);
+                            const double cj = ff_to_double(my_s, my_c);
                             I.T[j * I.ldt + k] = cj;
                             const double en = (j == piv) ? 0.0 : fmax(e_old - cj * cj, 0.0);
                             I.e[j] = en;
@@ -629,17 +636,22 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     ++g;
                 }
                 {
-                    const double be1 = __shfl_sync(0xffffffffu, best_e, 1);
-                    const int64_t bj1 = __shfl_sync(0xffffffffu, best_j, 1);
-                    const double es1 = __shfl_sync(0xffffffffu, esum, 1);
-                    if (lane == 0) {
+                    // the finalising lanes' candidates and sums (a fixed tree over lanes 0 .. CPW-1)
+#pragma unroll
+                    for (int o = 1; o < CPW; o <<= 1) {
+                        const double be1 = __shfl_xor_sync(0xffffffffu, best_e, o);
+                        const int64_t bj1 = __shfl_xor_sync(0xffffffffu, best_j, o);
+                        const double es1 = __shfl_xor_sync(0xffffffffu, esum, o);
                         if (better(be1, bj1, best_e, best_j)) {
                             best_e = be1;
                             best_j = bj1;
                         }
+                        esum += es1;
+                    }
+                    if (lane == 0) {
                         red[warp] = best_e;
                         redj[warp] = best_j;
-                        red[kBNW + warp] = esum + es1;
+                        red[kBNW + warp] = esum;
                     }
                 }
             }
@@ -719,9 +731,9 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
         for (uint32_t gc = ywait; gc < yiss; ++gc) mbar_wait(&ybar[gc % (uint32_t)kBNB], (gc / (uint32_t)kBNB) & 1u);
 }
 
-template <int P>
+template <int P, int CPW, int MT>
 size_t batch_smem() {
-    return (size_t)kBRingBytes + (size_t)(2 * BCfg<P>::SMAX + kBNB) * 8 + (size_t)2 * kBMaxRows * 4 + (size_t)kBMaxD * 8 +
+    return (size_t)kBRingBytes + (size_t)(2 * BCfg<P, CPW, MT>::SMAX + kBNB) * 8 + (size_t)2 * kBMaxRows * 4 + (size_t)kBMaxD * 8 +
            (size_t)2 * kBMaxD * 4 + (size_t)2 * kBNW * kBMaxLC * 4 + (size_t)(4 * kBNW + 16) * 8;
 }
 
@@ -734,6 +746,10 @@ struct rbd_batch_plan_s {
     int64_t count = 0;
     int64_t nslots = 0;
     int S = 0;
+    int cols = 16, tile_rows = 256, team_pct = 150;  // launch shape (rbd_batch_config)
+    std::vector<rbd_instance> inst;                  // the caller's descriptors (re-layout)
+    unsigned char* ws = nullptr;
+    size_t ws_bytes = 0;
     int num_sms = 0;
     size_t smem = 0;
     int init_blocks = 0;
@@ -766,9 +782,9 @@ rbd_status check_inst(const rbd_instance& I, rbd_dtype xt) {
 }
 
 // Team sizes: a matrix whose estimated work (passes over X for its expected number of bases -- the
-// caller's hint, else d_max -- plus the Gram-Schmidt streams) exceeds 2/3 of a CTA's fair share of
-// the batch gets ceil(1.5 work / share) members, at most 16, one column group and 128 rows per
-// member.
+// caller's hint, else d_max -- plus the Gram-Schmidt streams) is large against a CTA's fair share
+// of the batch gets ceil(team_pct / 100 * work / share) members (team_pct 150 by default), at most
+// 16, one column group and 128 rows per member.
 struct Plan {
     std::vector<int32_t> team;
     std::vector<int64_t> rb;
@@ -777,7 +793,7 @@ struct Plan {
     int64_t nslots = 0;
 };
 
-Plan make_plan(const rbd_instance* inst, int64_t count, int P, int ctas) {
+Plan make_plan(const rbd_instance* inst, int64_t count, int P, int ctas, int C, int team_pct) {
     Plan pl;
     pl.team.resize(count);
     pl.rb.resize(count);
@@ -792,9 +808,9 @@ Plan make_plan(const rbd_instance* inst, int64_t count, int P, int ctas) {
     const double share = total / std::max(1, ctas);
     for (int64_t i = 0; i < count; ++i) {
         const int64_t ldp = round_up(inst[i].m, 128);
-        const int64_t ng = ceil_div(inst[i].n, (int64_t)kBC);
+        const int64_t ng = ceil_div(inst[i].n, (int64_t)C);
         const int64_t tmax = std::max<int64_t>(1, std::min<int64_t>({16, ng, ldp / 128}));
-        int64_t t = (int64_t)std::ceil(1.5 * pl.cost[i] / share);
+        int64_t t = (int64_t)std::ceil(0.01 * team_pct * pl.cost[i] / share);
         t = std::max<int64_t>(1, std::min(t, tmax));
         pl.team[i] = (int32_t)t;
         pl.rb[i] = round_up(ceil_div(ldp, t), 32);
@@ -811,7 +827,7 @@ struct Layout {
     std::vector<size_t> planes, ys, e, xn2, hpart, nrm, vbuf, cand_e, cand_j, frop;
 };
 
-bool make_layout(const rbd_instance* inst, int64_t count, rbd_dtype xt, const Plan& pl, Layout& L) {
+bool make_layout(const rbd_instance* inst, int64_t count, rbd_dtype xt, const Plan& pl, int C, Layout& L) {
     const int P = (xt == RBD_F64) ? 2 : 1;
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -832,9 +848,9 @@ bool make_layout(const rbd_instance* inst, int64_t count, rbd_dtype xt, const Pl
     for (int64_t i = 0; i < count; ++i) {
         if (check_inst(inst[i], xt) != RBD_OK) return false;
         const int64_t ldp = round_up(inst[i].m, 128);
-        const int64_t ng = ceil_div(inst[i].n, (int64_t)kBC);
+        const int64_t ng = ceil_div(inst[i].n, (int64_t)C);
         const int64_t t = pl.team[i];
-        L.planes[i] = take((size_t)ng * kBC * P * ldp * 4);
+        L.planes[i] = take((size_t)ng * C * P * ldp * 4);
         L.ys[i] = take((size_t)t * 2 * inst[i].d_max * pl.rb[i] * 4);
         L.e[i] = take((size_t)inst[i].n * 8);
         L.xn2[i] = take((size_t)inst[i].n * 8);
@@ -857,6 +873,42 @@ rbd_status cuda_status(cudaError_t e) {
     return RBD_ECUDA;
 }
 
+// The kernel instances: storage (P = 2: FP64 as two planes, 1: FP32) x columns per warp (2, 4) x
+// tile rows (128, 256).
+struct BKernel {
+    const void* fn;
+    size_t smem;
+    int smax;
+};
+
+template <int P, int CPW, int MT>
+BKernel bkernel() {
+    return BKernel{(const void*)batch_kernel<P, CPW, MT>, batch_smem<P, CPW, MT>(), BCfg<P, CPW, MT>::SMAX};
+}
+
+BKernel kernel_for(int P, int cols, int tile_rows) {
+    const int i = (P == 2 ? 4 : 0) + (cols == 32 ? 2 : 0) + (tile_rows == 128 ? 1 : 0);
+    switch (i) {
+        case 0: return bkernel<1, 2, 256>();
+        case 1: return bkernel<1, 2, 128>();
+        case 2: return bkernel<1, 4, 256>();
+        case 3: return bkernel<1, 4, 128>();
+        case 4: return bkernel<2, 2, 256>();
+        case 5: return bkernel<2, 2, 128>();
+        case 6: return bkernel<2, 4, 256>();
+        default: return bkernel<2, 4, 128>();
+    }
+}
+
+constexpr int kColsOpt[2] = {16, 32};
+constexpr int kRowsOpt[2] = {256, 128};
+constexpr int kTeamOpt[3] = {150, 75, 300};
+
+bool valid_config(int cols, int tile_rows, int team_pct) {
+    return (cols == 16 || cols == 32) && (tile_rows == 128 || tile_rows == 256) &&
+           (team_pct == 75 || team_pct == 150 || team_pct == 300);
+}
+
 std::mutex g_battr_mu;
 bool g_battr_done[64] = {};
 
@@ -864,9 +916,13 @@ cudaError_t batch_setup(int dev) {
     std::lock_guard<std::mutex> lk(g_battr_mu);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (g_battr_done[dev]) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem<1>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem<2>());
+    cudaError_t e = cudaSuccess;
+    for (int P = 1; P <= 2 && e == cudaSuccess; ++P)
+        for (int cols : kColsOpt)
+            for (int rows : kRowsOpt) {
+                const BKernel k = kernel_for(P, cols, rows);
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+            }
     if (e == cudaSuccess) g_battr_done[dev] = true;
     return e;
 }
@@ -892,70 +948,54 @@ rbd_status run_with(rbd_batch_plan p, rbd_batch_result* results, cudaStream_t st
     bp.status = p->d_status;
     bp.res = results;
     bp.S = S;
+    bp.C = p->cols;
+    bp.MT = p->tile_rows;
     bp.wait_ns = wait_limit_ns(kWaitLimitNs);
     bp.team_ns = wait_limit_ns(kTeamWaitNs);
     cudaError_t e = cudaMemsetAsync(p->d_queue, 0, p->zero_bytes, st);
     if (e != cudaSuccess) return cuda_status(e);
     void* args[] = {&bp};
-    if (p->xt == RBD_F64) {
+    const int P = (p->xt == RBD_F64) ? 2 : 1;
+    const BKernel k = kernel_for(P, p->cols, p->tile_rows);
+    if (P == 2)
         batch_init_kernel<2><<<p->init_blocks, 256, 0, st>>>(bp);
-        e = cudaGetLastError();
-        if (e == cudaSuccess)
-            e = cudaLaunchCooperativeKernel((const void*)batch_kernel<2>, dim3((unsigned)p->num_sms), dim3(kBThreads), args,
-                                            p->smem, st);
-    } else {
+    else
         batch_init_kernel<1><<<p->init_blocks, 256, 0, st>>>(bp);
-        e = cudaGetLastError();
-        if (e == cudaSuccess)
-            e = cudaLaunchCooperativeKernel((const void*)batch_kernel<1>, dim3((unsigned)p->num_sms), dim3(kBThreads), args,
-                                            p->smem, st);
-    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel(k.fn, dim3((unsigned)p->num_sms), dim3(kBThreads), args, k.smem, st);
     return cuda_status(e);
 }
 
-}  // namespace
-
-extern "C" {
-
-size_t rbd_batch_workspace_bytes(const rbd_instance* inst, int64_t count, rbd_dtype xt) {
-    if (!inst || count < 1) return 0;
-    for (int64_t i = 0; i < count; ++i)
-        if (check_inst(inst[i], xt) != RBD_OK) return 0;
-    int sms = device_sms();
-    if (sms <= 0) sms = 160;  // no device: plan for a 160-SM part
-    const Plan pl = make_plan(inst, count, (xt == RBD_F64) ? 2 : 1, sms);
-    Layout L;
-    if (!make_layout(inst, count, xt, pl, L)) return 0;
-    return L.total;
+// Workspace of the layout every launch shape needs (the largest: the group width pads columns,
+// the team size sizes the member blocks and exchange buffers).
+size_t workspace_for_all(const rbd_instance* inst, int64_t count, rbd_dtype xt, int sms) {
+    const int P = (xt == RBD_F64) ? 2 : 1;
+    size_t most = 0;
+    for (int cols : kColsOpt)
+        for (int team : kTeamOpt) {
+            const Plan pl = make_plan(inst, count, P, sms, cols, team);
+            Layout L;
+            if (!make_layout(inst, count, xt, pl, cols, L)) return 0;
+            most = std::max(most, L.total);
+        }
+    return most;
 }
 
-rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst, int64_t count, rbd_dtype xt,
-                                 void* workspace, size_t workspace_bytes, void* stream) {
-    if (!plan || !inst || count < 1 || count > ((int64_t)1 << 30)) return RBD_EINVAL;
-    *plan = nullptr;
-    for (int64_t i = 0; i < count; ++i) {
-        const rbd_status s = check_inst(inst[i], xt);
-        if (s != RBD_OK) return s;
-    }
-    int dev = 0;
-    cudaError_t ce = cudaGetDevice(&dev);
-    if (ce != cudaSuccess) return cuda_status(ce);
-    int sms = 0, coop = 0;
-    ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (ce == cudaSuccess) ce = batch_setup(dev);
-    if (ce != cudaSuccess) {
-        cudaGetLastError();
-        return cuda_status(ce);
-    }
-    if (!coop) return RBD_EUNSUPPORTED;
+// Lay the plan's workspace out for a launch shape and upload the descriptor table (synchronises
+// the stream: the host vectors go out of scope).
+rbd_status plan_apply(rbd_batch_plan p, int cols, int tile_rows, int team_pct, int stages, cudaStream_t st) {
+    const rbd_dtype xt = (rbd_dtype)p->xt;
     const int P = (xt == RBD_F64) ? 2 : 1;
-    const Plan pl = make_plan(inst, count, P, sms);
+    const int64_t count = p->count;
+    const rbd_instance* inst = p->inst.data();
+    const Plan pl = make_plan(inst, count, P, p->num_sms, cols, team_pct);
     Layout L;
-    if (!make_layout(inst, count, xt, pl, L)) return RBD_EINVAL;
-    if (!workspace || ((uintptr_t)workspace & 255u) != 0) return RBD_EINVAL;
-    if (workspace_bytes < L.total) return RBD_ENOMEM;
-    unsigned char* base = (unsigned char*)workspace;
+    if (!make_layout(inst, count, xt, pl, cols, L)) return RBD_EINVAL;
+    if (L.total > p->ws_bytes) return RBD_ENOMEM;
+    const BKernel k = kernel_for(P, cols, tile_rows);
+    if (stages < 0 || stages == 1 || stages > k.smax) return RBD_EINVAL;
+    unsigned char* base = p->ws;
     std::vector<BInst> hi(count);
     std::vector<int64_t> colstart(count + 1, 0);
     for (int64_t i = 0; i < count; ++i) {
@@ -967,8 +1007,8 @@ rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst,
         b.n = s.n;
         b.ldx = s.ldx;
         b.ldp = round_up(s.m, 128);
-        b.ngroups = ceil_div(s.n, (int64_t)kBC);
-        b.NT = ceil_div(b.ldp, (int64_t)kBMT);
+        b.ngroups = ceil_div(s.n, (int64_t)cols);
+        b.NT = ceil_div(b.ldp, (int64_t)tile_rows);
         b.tol = s.tol;
         b.mode = s.mode;
         b.team = pl.team[i];
@@ -995,7 +1035,7 @@ rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst,
             b.cand_j = (int64_t*)(base + L.cand_j[i]);
             b.frop = (double*)(base + L.frop[i]);
         }
-        colstart[i + 1] = colstart[i] + b.ngroups * kBC;
+        colstart[i + 1] = colstart[i] + b.ngroups * cols;
     }
     std::vector<int32_t> slot_inst, slot_member;
     slot_inst.reserve(pl.nslots);
@@ -1005,28 +1045,25 @@ rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst,
             slot_inst.push_back(i);
             slot_member.push_back(b);
         }
-    cudaStream_t st = (cudaStream_t)stream;
-    ce = cudaMemcpyAsync(base + L.inst, hi.data(), (size_t)count * sizeof(BInst), cudaMemcpyHostToDevice, st);
+    cudaError_t ce = cudaMemcpyAsync(base + L.inst, hi.data(), (size_t)count * sizeof(BInst), cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(base + L.slot_inst, slot_inst.data(), (size_t)pl.nslots * 4, cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(base + L.slot_member, slot_member.data(), (size_t)pl.nslots * 4, cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(base + L.colstart, colstart.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // the host vectors go out of scope
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return cuda_status(ce);
     }
-    rbd_batch_plan p = new (std::nothrow) rbd_batch_plan_s();
-    if (!p) return RBD_ENOMEM;
-    p->xt = (int)xt;
-    p->count = count;
     p->nslots = pl.nslots;
-    p->S = (P == 2) ? BCfg<2>::SMAX : BCfg<1>::SMAX;
-    p->num_sms = sms;
-    p->smem = (P == 2) ? batch_smem<2>() : batch_smem<1>();
-    p->init_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(colstart[count], 8), (int64_t)sms * 8));
+    p->cols = cols;
+    p->tile_rows = tile_rows;
+    p->team_pct = team_pct;
+    p->S = stages ? stages : k.smax;
+    p->smem = k.smem;
+    p->init_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(colstart[count], 8), (int64_t)p->num_sms * 8));
     p->d_inst = (BInst*)(base + L.inst);
     p->d_slot_inst = (int32_t*)(base + L.slot_inst);
     p->d_slot_member = (int32_t*)(base + L.slot_member);
@@ -1034,6 +1071,59 @@ rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst,
     p->d_queue = (uint32_t*)(base + L.queue);
     p->d_status = (int32_t*)(base + L.status);
     p->zero_bytes = L.per_begin;
+    return RBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rbd_batch_workspace_bytes(const rbd_instance* inst, int64_t count, rbd_dtype xt) {
+    if (!inst || count < 1) return 0;
+    for (int64_t i = 0; i < count; ++i)
+        if (check_inst(inst[i], xt) != RBD_OK) return 0;
+    int sms = device_sms();
+    if (sms <= 0) sms = 160;  // no device: plan for a 160-SM part
+    return workspace_for_all(inst, count, xt, sms);
+}
+
+rbd_status rbd_batch_plan_create(rbd_batch_plan* plan, const rbd_instance* inst, int64_t count, rbd_dtype xt,
+                                 void* workspace, size_t workspace_bytes, void* stream) {
+    if (!plan || !inst || count < 1 || count > ((int64_t)1 << 30)) return RBD_EINVAL;
+    *plan = nullptr;
+    for (int64_t i = 0; i < count; ++i) {
+        const rbd_status s = check_inst(inst[i], xt);
+        if (s != RBD_OK) return s;
+    }
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    int sms = 0, coop = 0;
+    ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (ce == cudaSuccess) ce = batch_setup(dev);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(ce);
+    }
+    if (!coop) return RBD_EUNSUPPORTED;
+    const size_t need = workspace_for_all(inst, count, xt, sms);
+    if (need == 0) return RBD_EINVAL;
+    if (!workspace || ((uintptr_t)workspace & 255u) != 0) return RBD_EINVAL;
+    if (workspace_bytes < need) return RBD_ENOMEM;
+    rbd_batch_plan p = new (std::nothrow) rbd_batch_plan_s();
+    if (!p) return RBD_ENOMEM;
+    p->xt = (int)xt;
+    p->count = count;
+    p->num_sms = sms;
+    p->inst.assign(inst, inst + count);
+    p->ws = (unsigned char*)workspace;
+    p->ws_bytes = workspace_bytes;
+    const rbd_status rs = plan_apply(p, 16, 256, 150, 0, (cudaStream_t)stream);
+    if (rs != RBD_OK) {
+        delete p;
+        return rs;
+    }
     *plan = p;
     return RBD_OK;
 }
@@ -1043,43 +1133,87 @@ rbd_status rbd_batch_run(rbd_batch_plan plan, rbd_batch_result* results, void* s
     return run_with(plan, results, (cudaStream_t)stream, plan->S);
 }
 
-rbd_status rbd_batch_tune(rbd_batch_plan plan, rbd_batch_result* results, void* stream, int32_t* stages_out) {
+rbd_status rbd_batch_tune(rbd_batch_plan plan, rbd_batch_result* results, void* stream, rbd_batch_config* chosen) {
     if (!plan || !results) return RBD_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    const int smax = (plan->xt == RBD_F64) ? BCfg<2>::SMAX : BCfg<1>::SMAX;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
         if (e0) cudaEventDestroy(e0);
         return RBD_ECUDA;
     }
-    rbd_status rs = run_with(plan, results, st, plan->S);  // warm-up
-    float best = 1e30f;
-    int best_s = plan->S;
-    for (int s = 2; s <= smax && rs == RBD_OK; s += (smax >= 6 ? 2 : 1)) {
+    const int P = (plan->xt == RBD_F64) ? 2 : 1;
+    // one run (the first of a shape warms it up), timed
+    auto timed = [&](int S, float& ms) -> rbd_status {
+        rbd_status rs = run_with(plan, results, st, S);
+        if (rs != RBD_OK) return rs;
         cudaEventRecord(e0, st);
-        rs = run_with(plan, results, st, s);
+        rs = run_with(plan, results, st, S);
         cudaEventRecord(e1, st);
-        if (rs != RBD_OK) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rs = RBD_ECUDA;
-            break;
+        if (rs != RBD_OK) return rs;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return RBD_ECUDA;
+        return RBD_OK;
+    };
+    rbd_status rs = RBD_OK;
+    float best = 1e30f;
+    int bc = plan->cols, br = plan->tile_rows, bt = plan->team_pct;
+    // every launch shape at its deepest ring
+    for (int cols : kColsOpt)
+        for (int rows : kRowsOpt)
+            for (int team : kTeamOpt) {
+                if (rs != RBD_OK) break;
+                rs = plan_apply(plan, cols, rows, team, 0, st);
+                float ms = 0.f;
+                if (rs == RBD_OK) rs = timed(plan->S, ms);
+                if (rs == RBD_OK && ms < best) {
+                    best = ms;
+                    bc = cols;
+                    br = rows;
+                    bt = team;
+                }
+            }
+    // the ring depths of the fastest shape
+    int bs = 0;
+    if (rs == RBD_OK) rs = plan_apply(plan, bc, br, bt, 0, st);
+    if (rs == RBD_OK) {
+        const int smax = kernel_for(P, bc, br).smax;
+        float best_s = best;
+        for (int s = 2; s < smax && rs == RBD_OK; s = (s < 4) ? s + 1 : 2 * s) {
+            float ms = 0.f;
+            rs = timed(s, ms);
+            if (rs == RBD_OK && ms < best_s) {
+                best_s = ms;
+                bs = s;
+            }
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_s = s;
+    }
+    if (rs == RBD_OK) {
+        plan->S = bs ? bs : kernel_for(P, bc, br).smax;
+        if (chosen) {
+            chosen->cols = bc;
+            chosen->tile_rows = br;
+            chosen->team_pct = bt;
+            chosen->stages = plan->S;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rs == RBD_OK) {
-        plan->S = best_s;
-        if (stages_out) *stages_out = best_s;
-    }
     cudaGetLastError();
     return rs;
+}
+
+rbd_status rbd_batch_plan_config(rbd_batch_plan plan, rbd_batch_config* cfg) {
+    if (!plan || !cfg) return RBD_EINVAL;
+    cfg->cols = plan->cols;
+    cfg->tile_rows = plan->tile_rows;
+    cfg->team_pct = plan->team_pct;
+    cfg->stages = plan->S;
+    return RBD_OK;
+}
+
+rbd_status rbd_batch_plan_set_config(rbd_batch_plan plan, const rbd_batch_config* cfg, void* stream) {
+    if (!plan || !cfg || !valid_config(cfg->cols, cfg->tile_rows, cfg->team_pct)) return RBD_EINVAL;
+    return plan_apply(plan, cfg->cols, cfg->tile_rows, cfg->team_pct, cfg->stages, (cudaStream_t)stream);
 }
 
 rbd_status rbd_batch_plan_destroy(rbd_batch_plan plan) {

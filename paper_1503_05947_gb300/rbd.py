@@ -46,6 +46,11 @@ class _Profile(ctypes.Structure):
                 ("loop_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class _BatchConfig(ctypes.Structure):
+    _fields_ = [("cols", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("team_pct", ctypes.c_int32),
+                ("stages", ctypes.c_int32)]
+
+
 class _Instance(ctypes.Structure):
     _fields_ = [("X", _PTR), ("m", _I64), ("n", _I64), ("ldx", _I64), ("tol", _DBL), ("mode", ctypes.c_int32),
                 ("d_hint", ctypes.c_int32), ("d_max", _I64), ("start", _I64), ("Y", _PTR), ("ldy", _I64),
@@ -107,7 +112,11 @@ def load():
     lib.rbd_batch_run.restype = ctypes.c_int
     lib.rbd_batch_run.argtypes = [_PTR, _PTR, _PTR]
     lib.rbd_batch_tune.restype = ctypes.c_int
-    lib.rbd_batch_tune.argtypes = [_PTR, _PTR, _PTR, ctypes.POINTER(ctypes.c_int32)]
+    lib.rbd_batch_tune.argtypes = [_PTR, _PTR, _PTR, ctypes.POINTER(_BatchConfig)]
+    lib.rbd_batch_plan_config.restype = ctypes.c_int
+    lib.rbd_batch_plan_config.argtypes = [_PTR, ctypes.POINTER(_BatchConfig)]
+    lib.rbd_batch_plan_set_config.restype = ctypes.c_int
+    lib.rbd_batch_plan_set_config.argtypes = [_PTR, ctypes.POINTER(_BatchConfig), _PTR]
     lib.rbd_batch_plan_destroy.restype = ctypes.c_int
     lib.rbd_batch_plan_destroy.argtypes = [_PTR]
     lib.rbd_compress_batched.restype = ctypes.c_int
@@ -542,12 +551,63 @@ class BatchPlan:
         with torch.cuda.device(self.device):
             _check(load().rbd_batch_run(self._plan, self.res.data_ptr(), _stream_ptr(self.device)), "rbd_batch_run")
 
-    def tune(self) -> int:
-        stages = ctypes.c_int32(0)
+    def tune(self, cache: Optional[str] = None) -> dict:
+        """Autotune the launch shape (rbd_batch_tune) and keep it in the plan; returns the choice
+        {cols, tile_rows, team_pct, stages} plus "cached": whether it came from `cache`.
+
+        ``cache``: a JSON file of earlier choices keyed by ``bucket()``.  A batch whose bucket is
+        there takes the stored shape without timing anything; otherwise the tuner runs and the
+        choice is added to the file."""
+        import json
+        key = self.bucket()
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                cfg = dict(table[key])
+                self.set_config(cfg)
+                return dict(cfg, cached=True)
+        c = _BatchConfig()
         with torch.cuda.device(self.device):
-            _check(load().rbd_batch_tune(self._plan, self.res.data_ptr(), _stream_ptr(self.device),
-                                         ctypes.byref(stages)), "rbd_batch_tune")
-        return int(stages.value)
+            _check(load().rbd_batch_tune(self._plan, self.res.data_ptr(), _stream_ptr(self.device), ctypes.byref(c)),
+                   "rbd_batch_tune")
+        cfg = {f: int(getattr(c, f)) for f, _ in _BatchConfig._fields_}
+        if cache:
+            table = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    table = json.load(f)
+            table[key] = cfg
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(cfg, cached=False)
+
+    def config(self) -> dict:
+        c = _BatchConfig()
+        _check(load().rbd_batch_plan_config(self._plan, ctypes.byref(c)), "rbd_batch_plan_config")
+        return {f: int(getattr(c, f)) for f, _ in _BatchConfig._fields_}
+
+    def set_config(self, cfg: dict) -> None:
+        c = _BatchConfig(int(cfg["cols"]), int(cfg["tile_rows"]), int(cfg["team_pct"]), int(cfg.get("stages", 0)))
+        with torch.cuda.device(self.device):
+            _check(load().rbd_batch_plan_set_config(self._plan, ctypes.byref(c), _stream_ptr(self.device)),
+                   "rbd_batch_plan_set_config")
+
+    def bucket(self) -> str:
+        """The tuning cache's key for this batch: storage type, the GPU's SM count, the batch size
+        and the quartiles of rows, columns and d_max (each rounded to a power of two)."""
+        import numpy as np
+
+        def q(v):
+            return [int(2 ** round(np.log2(max(1, x)))) for x in np.percentile(v, [25, 50, 75])]
+        ms = [it["X"].shape[0] for it in self.items]
+        ns = [it["X"].shape[1] for it in self.items]
+        ds = [int(it.get("d_hint") or it["d_max"]) for it in self.items]
+        sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        return (f"{'f64' if self.dtype == torch.float64 else 'f32'}/sm{sms}/count{2 ** round(np.log2(len(ms)))}"
+                f"/m{q(ms)}/n{q(ns)}/d{q(ds)}").replace(" ", "")
 
     def results(self) -> list:
         import numpy as np

@@ -4,9 +4,10 @@ and modes in one persistent launch, each against the FP64 oracle on the same sto
 Bar per matrix (float-float dot products, as the plain form): identical d and pivots; Y, T, err
 and nu within 1e-10 (normwise), in cases whose steps keep nu / ||x_i|| above ~1e-3 (the two
 sides' rounding is amplified by ||x_i|| / nu at each step and compounds over the steps; see
-test_gpu_precision.py).  Also: a run captured in a CUDA graph and replayed gives the same
-bits, the autotuner's choice does not change the results, a non-finite matrix fails alone, and
-the full 2048-matrix workload on sampled matrices.
+test_gpu_precision.py).  Also: the autotuned launch shape matches the default one to the bar,
+a tuned run captured in a CUDA graph and replayed gives the same bits, tile rows and ring depth
+leave every bit unchanged, a non-finite matrix fails alone, and the full 2048-matrix workload on
+sampled matrices.
 """
 import numpy as np
 import pytest
@@ -88,17 +89,52 @@ def test_batch_equals_single_matrix_path(rbd):
             assert (c.T - s.T).abs().max().item() <= TOL * scale
 
 
-def test_graph_replay_and_tuner_keep_the_bits(rbd):
+def _snapshot(plan):
+    torch.cuda.synchronize()
+    return plan.res.clone(), [(o["T"].clone(), o["Y"].clone(), o["pivots"].clone()) for o in plan.out], plan.results()
+
+
+def _same_bits(plan, snap):
+    res, outs, _ = snap
+    assert torch.equal(plan.res, res)
+    for i, (o, (T, Y, piv)) in enumerate(zip(plan.out, outs)):
+        d = plan.results()[i]["d"]
+        assert torch.equal(o["T"][:d], T[:d]) and torch.equal(o["Y"][:, :d], Y[:, :d]), i
+        assert torch.equal(o["pivots"][:d], piv[:d]), i
+
+
+def _close(plan, snap, items):
+    """The same d and pivots, Y and T within the parity bar (a launch shape regroups sums)."""
+    _, outs, ref = snap
+    got = plan.results()
+    for i, (o, (T, Y, piv)) in enumerate(zip(plan.out, outs)):
+        d = got[i]["d"]
+        assert d == ref[i]["d"] and got[i]["status"] == 0, i
+        assert torch.equal(o["pivots"][:d], piv[:d]), i
+        scale = torch.linalg.vector_norm(items[i]["X"].double(), dim=0).max().item()
+        assert (o["Y"][:, :d] - Y[:, :d]).abs().max().item() <= TOL, i
+        assert (o["T"][:d] - T[:d]).abs().max().item() <= TOL * scale, i
+
+
+def test_tuned_plan_and_graph_replay(rbd, tmp_path):
+    """The autotuner's choice (group width, tile rows, team size, ring depth) is kept in the plan
+    and in the JSON cache under the batch's bucket; the tuned plan matches the default one to the
+    parity bar, and a run of it captured in a CUDA graph and replayed gives its exact bits."""
     items, _ = mixed_batch(torch.float32, 14)
     plan = rbd.BatchPlan(items)
+    assert plan.config() == {"cols": 16, "tile_rows": 256, "team_pct": 150, "stages": plan.config()["stages"]}
     plan.run()
-    torch.cuda.synchronize()
-    ref = [(o["T"].clone(), o["Y"].clone(), o["pivots"].clone()) for o in plan.out]
-    ref_res = plan.res.clone()
-    stages = plan.tune()
-    assert stages >= 2
-    assert torch.equal(plan.res, ref_res)
-    for o, (T, Y, piv) in zip(plan.out, ref):
+    default = _snapshot(plan)
+    cache = str(tmp_path / "tune.json")
+    cfg = plan.tune(cache=cache)
+    assert not cfg["cached"]
+    assert cfg["cols"] in (16, 32) and cfg["tile_rows"] in (128, 256) and cfg["team_pct"] in (75, 150, 300)
+    assert cfg["stages"] >= 2
+    assert plan.config() == {k: cfg[k] for k in ("cols", "tile_rows", "team_pct", "stages")}
+    plan.run()
+    tuned = _snapshot(plan)
+    _close(plan, default, items)
+    for o in plan.out:
         o["T"].zero_()
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
@@ -112,11 +148,36 @@ def test_graph_replay_and_tuner_keep_the_bits(rbd):
     for o in plan.out:
         o["T"].zero_()
     g.replay()
-    torch.cuda.synchronize()
-    assert torch.equal(plan.res, ref_res)
-    for i, (o, (T, Y, piv)) in enumerate(zip(plan.out, ref)):
-        d = plan.results()[i]["d"]
-        assert torch.equal(o["T"][:d], T[:d]) and torch.equal(o["Y"][:, :d], Y[:, :d]), i
+    _same_bits(plan, tuned)
+    # a second plan over the same batch takes the cached shape without timing
+    plan2 = rbd.BatchPlan(items)
+    cfg2 = plan2.tune(cache=cache)
+    assert cfg2["cached"] and {k: cfg2[k] for k in plan2.config()} == plan2.config()
+    plan2.run()
+    _same_bits(plan2, tuned)
+
+
+def test_every_launch_shape_matches(rbd):
+    """Every launch shape gives the default plan's d and pivots and its Y and T to the parity bar;
+    the tile rows and ring depth alone leave every bit unchanged."""
+    items, _ = mixed_batch(torch.float64, 16)
+    plan = rbd.BatchPlan(items)
+    plan.run()
+    default = _snapshot(plan)
+    for cols in (16, 32):
+        for team in (75, 150, 300):
+            base = None
+            for rows in (256, 128):
+                for stages in (0, 2):
+                    plan.set_config({"cols": cols, "tile_rows": rows, "team_pct": team, "stages": stages})
+                    plan.run()
+                    _close(plan, default, items)
+                    if base is None:
+                        base = _snapshot(plan)
+                    else:
+                        _same_bits(plan, base)
+    with pytest.raises(rbd.RbdError):
+        plan.set_config({"cols": 24, "tile_rows": 256, "team_pct": 150})
 
 
 def test_nonfinite_matrix_fails_alone(rbd, oracle_mod):
