@@ -76,7 +76,7 @@ def measured_peaks() -> dict:
 def ncu_traffic() -> dict | None:
     """DRAM bytes per launch of the persistent loop kernel on this workload, from the committed
     ncu summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "loop_kernel_image8192_f64_traffic.json")
+    p = os.path.join(ROOT, "profiles", "defer_kernel_image8192_f64_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -708,10 +708,12 @@ def batched_forms(dev) -> dict:
     return out
 
 
-def profile_case(name: str):
+def profile_case(name: str, shape: str | None = None):
     """Short, fixed launches of one kernel for profiler captures (not a bench line):
     bf16-small: the persistent kernel on the parametric snapshots 16384 x 4096 stored in BF16;
-    batched-small: the batched form on the first 256 matrices of the 2048-matrix workload."""
+    batched-small / batched-full: two runs of the batched form on the first 256 matrices / all 2048
+    of the 2048-matrix workload, in the launch shape `shape` ("cols,tile_rows,team_pct,stages"; the
+    plan's default without it)."""
     import torch
 
     import gen
@@ -723,18 +725,24 @@ def profile_case(name: str):
             r = rbd.compress(X, 0.0, 32)
         torch.cuda.synchronize(dev)
         print(json.dumps({"case": name, "bases": r.d}))
-    elif name == "batched-small":
+    elif name in ("batched-small", "batched-full"):
         items = []
-        for sp in gen.batch_specs(2048, seed=3)[:256]:
+        for sp in gen.batch_specs(2048, seed=3)[:256 if name == "batched-small" else 2048]:
             s = gen.decay_spectrum(sp["rate"], min(sp["m"], sp["n"]))
             X = gen.lowrank_torch(sp["m"], sp["n"], s, sp["seed"], device=dev, dtype=torch.float32)
             items.append({"X": X, "tol": sp["tol"], "tol_mode": "maxcol_rel", "d_max": sp["d_max"],
                           "d_hint": sp["d_hint"]})
         plan = rbd.BatchPlan(items)
+        if shape:
+            c, r_, t, st = (int(v) for v in shape.split(","))
+            plan.set_config({"cols": c, "tile_rows": r_, "team_pct": t, "stages": st})
         for _ in range(2):
             plan.run()
         torch.cuda.synchronize(dev)
-        print(json.dumps({"case": name, "bases": int(sum(r["d"] for r in plan.results()))}))
+        res = plan.results()
+        xbytes = 4.0 * sum((r["d"] + 1) * it["X"].shape[0] * it["X"].shape[1] for r, it in zip(res, items))
+        print(json.dumps({"case": name, "shape": plan.config(), "bases": int(sum(r["d"] for r in res)),
+                          "x_bytes_streamed_per_run": xbytes}))
     else:
         raise SystemExit(f"unknown profile case {name}")
 
@@ -757,11 +765,12 @@ def main():
                     help="basis limit; values below 512 give the short profiling case, not a bench line")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (end-to-end) measurement")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / batched form measurements")
-    ap.add_argument("--profile-case", choices=["bf16-small", "batched-small"], default=None,
+    ap.add_argument("--batch-shape", default=None, help="cols,tile_rows,team_pct,stages for the batched profile cases")
+    ap.add_argument("--profile-case", choices=["bf16-small", "batched-small", "batched-full"], default=None,
                     help="run one short fixed case for a profiler capture instead of the bench")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case)
+        profile_case(args.profile_case, args.batch_shape)
         return
     world, rank, local = dist_setup()
     global D_MAX
