@@ -65,8 +65,9 @@ def test_noalloc_matches_compress_twice(rbd, case):
     ref = _host(rbd.compress(X, tol, d_max, start=start, tol_mode=mode))
     assert ref["d"] >= 2
     for call in range(2):
-        got = _host(rbd.compress_noalloc(X, tol, d_max, start=start, tol_mode=mode))
-        _close(Xn, got, ref, f"{name}, call {call + 1}")
+        r = rbd.compress_noalloc(X, tol, d_max, start=start, tol_mode=mode)
+        _close(Xn, _host(r), ref, f"{name}, call {call + 1}")
+        assert r.launches == 2  # the initial pass and the persistent loop kernel
 
 
 def test_noalloc_preallocated_outputs(rbd):
@@ -111,4 +112,8 @@ def test_noalloc_stepwise_path(rbd, monkeypatch):
     ref = _host(rbd.compress(X, 1e-3, 64))
     assert 2 <= ref["d"] < 64  # stops on the tolerance, so later launches return at entry
     for call in range(2):
-        _close(Xn, _host(rbd.compress_noalloc(X, 1e-3, 64)), ref, f"stepwise, call {call + 1}")
+        got = rbd.compress_noalloc(X, 1e-3, 64)
+        _close(Xn, _host(got), ref, f"stepwise, call {call + 1}")
+        # every step up to d_max is enqueued (init, then per step the orthogonalisation kernels
+        # and the pass): 4 d_max + 3 launches, whatever step the device stopped at
+        assert got.launches == 4 * 64 + 3
