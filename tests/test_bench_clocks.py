@@ -72,7 +72,7 @@ def test_traffic_is_reported_only_for_the_sources_it_was_taken_on(tmp_path, monk
         shutil.copy(os.path.join(ROOT, rel), dst)
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    path = tmp_path / "profiles" / "loop_kernel_image8192_f64_traffic.json"
+    path = tmp_path / "profiles" / "defer_kernel_image8192_f64_traffic.json"
     path.write_text(json.dumps({"source_hash": bench.pass_kernel_hash(), "dram_bytes_per_launch": 1.0}))
     assert bench.ncu_traffic()["dram_bytes_per_launch"] == 1.0
     with open(tmp_path / bench.PASS_SOURCES[0], "a") as f:
