@@ -365,6 +365,8 @@ def run_gpu(args, world, rank, local):
         forms["precision"] = precision_forms(dev, peaks)
         forms["batched"] = batched_forms(dev)
         forms["paper_5001"] = paper_5001_form(dev)
+        forms["small"] = small_form(dev)
+        forms["grad"] = grad_form(dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -565,6 +567,95 @@ def precision_forms(dev, peaks: dict) -> dict:
         vs[k] = {"bases": r.d, "rel_err": e, "rel_err_over_oracle": e / e_or, "rel_err_minus_oracle": e - e_or}
     out["vs_oracle"] = vs
     return out
+
+
+def small_form(dev) -> dict:
+    """The small FP64 workload (1024 x 512 = U diag(s) V' with s_i = 2^(-i/4), noise sd 1e-5, d_max
+    64, tol 1e-6 on the max column residual): one rbd_compress on the device (CUDA events, median
+    of 10 calls, X resident; X fits in L2, so the rate is an effective one), the FP64 oracle on one
+    host core and on all of them, and the largest deviations from the oracle."""
+    import statistics
+
+    import torch
+
+    import gen
+    import oracle
+    import paper_1503_05947_gb300 as rbd
+    Xn = gen.decay_matrix_c1(seed=0, noise_sigma=1e-5)
+    m, n = Xn.shape
+    X = torch.from_numpy(np.ascontiguousarray(Xn.T)).to(dev).t()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ts = []
+    for i in range(12):
+        torch.cuda.synchronize(dev)
+        ev0.record()
+        r = rbd.compress(X, 1e-6, 64)
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        if i >= 2:
+            ts.append(ev0.elapsed_time(ev1))
+    ms = statistics.median(ts)
+    t0 = time.perf_counter()
+    ref = oracle.compress(Xn, 1e-6, 64)
+    t1 = time.perf_counter() - t0
+    nth = host_cpu()["cores"] if omp_available() else 0
+    t0 = time.perf_counter()
+    oracle.compress(Xn, 1e-6, 64, threads=nth)
+    tall = time.perf_counter() - t0
+    scale = np.linalg.norm(Xn, axis=0)
+    Y = r.Y.cpu().numpy()
+    T = r.T.cpu().numpy()
+    return {"workload": "1024x512 U diag(2^(-i/4)) V' + N(0, 1e-10) noise (sd 1e-5), FP64, d_max 64, tol 1e-6 max column",
+            "bases": r.d, "ms": ms, "effective_gbs": (r.d + 1) * m * n * 8 / (ms * 1e-3) / 1e9,
+            "note": "X (4 MiB) is L2-resident: an effective rate, not an HBM one",
+            "pivots_equal_oracle": bool(np.array_equal(r.pivots.cpu().numpy(), ref["pivots"])),
+            "max_dY": float(np.linalg.norm(Y - ref["Y"], axis=0).max()),
+            "max_dT_rel": float((np.abs(T - ref["T"]) / scale[None, :]).max()),
+            "oracle_s_1core": t1, "oracle_s_all_cores": tall, "oracle_threads": max(nth, 1)}
+
+
+def grad_form(dev) -> dict:
+    """The differentiation workload: 64 FP32 matrices 1024 x 512 (decay 0.1), d = 32, 256
+    out-of-sample vectors each.  Device time of the forward compressions and of the adjoints
+    (rbd_grad: loss and gradient), CUDA events over the 64 instances; the oracle's adjoint on two
+    instances (one host core), scaled to 64, and the largest deviation from it."""
+    import torch
+
+    import gen
+    import oracle
+    import paper_1503_05947_gb300 as rbd
+    inst = []
+    for i in range(64):
+        X = gen.lowrank_haar(1024, 512, np.exp(-0.1 * np.arange(512)), seed=1000 + i).astype(np.float32)
+        Xo = gen.out_of_sample(1024, 256, seed=2000 + i).astype(np.float32)
+        inst.append((torch.from_numpy(np.ascontiguousarray(X.T)).to(dev).t(),
+                     torch.from_numpy(np.ascontiguousarray(Xo.T)).to(dev).t()))
+    for X, Xo in inst[:2]:
+        r = rbd.compress(X, 0.0, 32)
+        rbd.grad(X, r.Y, r.T, r.pivots, Xo)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize(dev)
+    e[0].record()
+    fw = [rbd.compress(X, 0.0, 32) for X, _ in inst]
+    e[1].record()
+    outs = [rbd.grad(X, r.Y, r.T, r.pivots, Xo) for (X, Xo), r in zip(inst, fw)]
+    e[2].record()
+    torch.cuda.synchronize(dev)
+    worst, t_or = 0.0, 0.0
+    for i in (0, 37):
+        X, Xo = inst[i]
+        r = fw[i]
+        t0 = time.perf_counter()
+        Gref, _ = oracle.grad(X.double().cpu().numpy(), r.Y.cpu().numpy(), r.T.cpu().numpy(), r.pivots.cpu().numpy(),
+                              Xo.double().cpu().numpy())
+        t_or += time.perf_counter() - t0
+        G = outs[i][0].cpu().numpy()
+        worst = max(worst, float(np.abs(G - Gref).max() / np.abs(Gref).max()))
+    return {"workload": "64 FP32 matrices 1024x512 (decay 0.1), d = 32, 256 out-of-sample vectors each",
+            "forward_ms": e[0].elapsed_time(e[1]), "adjoint_ms": e[1].elapsed_time(e[2]),
+            "adjoint_max_rel_dev_vs_oracle": worst, "oracle_adjoint_s_1core_est_64": t_or / 2 * 64,
+            "fd_check": "against FP64 central differences in tests/test_gpu_grad.py (<= 1e-6 relative)"}
 
 
 PAPER5001_N, PAPER5001_D = 5001, 22

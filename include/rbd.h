@@ -209,9 +209,13 @@ rbd_status rbd_compress_rows(const void* X, rbd_dtype xt, int64_t m, int64_t n, 
  *  d_max       [in]  the new limit; Y, T, pivots, err, nu must have capacity d_max, and hold the
  *                    first d0 columns / rows / entries.
  *  The running indicator e_j, the Frobenius residual and the split copy of Y are rebuilt from
- *  Y(:, 0:d0), T(0:d0, :) and pivots with the operations and order the loop used, so the
- *  continued run gives the results of one rbd_compress call with this d_max (the same bits, on
- *  the same path).  err[d0 - 1] is rewritten (certified again); entries from d0 on are new.
+ *  Y(:, 0:d0), T(0:d0, :) and pivots with the operations and order the loop used.  On the
+ *  stepwise path the continued run then gives the bits of one rbd_compress call with this d_max.
+ *  The persistent two-barrier kernel forms each basis at the start of the next one (its second
+ *  Gram-Schmidt sweep is deferred); resumed at d0 it takes basis d0 - 1 as the caller's Y holds
+ *  it, so the continued run has the same pivots, d and stop as one call, and Y, T, err and nu
+ *  equal to its accuracy rather than bit for bit.  err[d0 - 1] is rewritten (certified again);
+ *  entries from d0 on are new.
  *  Errors: those of rbd_compress, and RBD_EINVAL for d0 or next_pivot out of range.
  */
 rbd_status rbd_compress_resume(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t ldx,
