@@ -617,9 +617,10 @@ def small_form(dev) -> dict:
 
 def grad_form(dev) -> dict:
     """The differentiation workload: 64 FP32 matrices 1024 x 512 (decay 0.1), d = 32, 256
-    out-of-sample vectors each.  Device time of the forward compressions and of the adjoints
-    (rbd_grad: loss and gradient), CUDA events over the 64 instances; the oracle's adjoint on two
-    instances (one host core), scaled to 64, and the largest deviation from it."""
+    out-of-sample vectors each.  Device time (CUDA events) of the 64 forward compressions and of
+    the 64 adjoints (loss and gradient), as a batch (one batched compression launch, one
+    rbd_grad_batched call) and one instance at a time (rbd_compress, rbd_grad); the oracle's adjoint
+    on two instances (one host core), scaled to 64, and the largest deviation from it."""
     import torch
 
     import gen
@@ -631,6 +632,7 @@ def grad_form(dev) -> dict:
         Xo = gen.out_of_sample(1024, 256, seed=2000 + i).astype(np.float32)
         inst.append((torch.from_numpy(np.ascontiguousarray(X.T)).to(dev).t(),
                      torch.from_numpy(np.ascontiguousarray(Xo.T)).to(dev).t()))
+    # one instance at a time
     for X, Xo in inst[:2]:
         r = rbd.compress(X, 0.0, 32)
         rbd.grad(X, r.Y, r.T, r.pivots, Xo)
@@ -642,7 +644,29 @@ def grad_form(dev) -> dict:
     outs = [rbd.grad(X, r.Y, r.T, r.pivots, Xo) for (X, Xo), r in zip(inst, fw)]
     e[2].record()
     torch.cuda.synchronize(dev)
-    worst, t_or = 0.0, 0.0
+    one = (e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]))
+    # as a batch
+    plan = rbd.BatchPlan([{"X": X, "tol": 0.0, "d_max": 32} for X, _ in inst])
+    plan.run()
+    res = plan.results()
+    gi = []
+    for i, ((X, Xo), r) in enumerate(zip(inst, res)):
+        c = plan.compressed(i, r)
+        gi.append({"X": X, "Y": c.Y, "T": c.T, "pivots": c.pivots, "Xo": Xo})
+    rbd.grad_batched(gi)
+    torch.cuda.synchronize(dev)
+    fb, ab = [], []
+    for _ in range(3):
+        e[0].record()
+        plan.run()
+        e[1].record()
+        bouts = rbd.grad_batched(gi)
+        e[2].record()
+        torch.cuda.synchronize(dev)
+        fb.append(e[0].elapsed_time(e[1]))
+        ab.append(e[1].elapsed_time(e[2]))
+    same_piv = all(torch.equal(g["pivots"], r.pivots) for g, r in zip(gi, fw))
+    worst, worst_b, t_or = 0.0, 0.0, 0.0
     for i in (0, 37):
         X, Xo = inst[i]
         r = fw[i]
@@ -650,11 +674,19 @@ def grad_form(dev) -> dict:
         Gref, _ = oracle.grad(X.double().cpu().numpy(), r.Y.cpu().numpy(), r.T.cpu().numpy(), r.pivots.cpu().numpy(),
                               Xo.double().cpu().numpy())
         t_or += time.perf_counter() - t0
-        G = outs[i][0].cpu().numpy()
-        worst = max(worst, float(np.abs(G - Gref).max() / np.abs(Gref).max()))
+        worst = max(worst, float(np.abs(outs[i][0].cpu().numpy() - Gref).max() / np.abs(Gref).max()))
+        g = gi[i]
+        Gb, _ = oracle.grad(X.double().cpu().numpy(), g["Y"].cpu().numpy(), g["T"].cpu().numpy(),
+                            g["pivots"].cpu().numpy(), Xo.double().cpu().numpy())
+        worst_b = max(worst_b, float(np.abs(bouts[i][0].cpu().numpy() - Gb).max() / np.abs(Gb).max()))
+    del plan
     return {"workload": "64 FP32 matrices 1024x512 (decay 0.1), d = 32, 256 out-of-sample vectors each",
-            "forward_ms": e[0].elapsed_time(e[1]), "adjoint_ms": e[1].elapsed_time(e[2]),
-            "adjoint_max_rel_dev_vs_oracle": worst, "oracle_adjoint_s_1core_est_64": t_or / 2 * 64,
+            "batched": {"forward_ms": float(np.median(fb)), "adjoint_ms": float(np.median(ab)),
+                        "note": "one batched compression launch (tol 0, d_max 32) and one rbd_grad_batched call "
+                                "(through the Python binding), median of 3",
+                        "pivots_equal_one_by_one": same_piv, "adjoint_max_rel_dev_vs_oracle": worst_b},
+            "one_by_one": {"forward_ms": one[0], "adjoint_ms": one[1], "adjoint_max_rel_dev_vs_oracle": worst},
+            "oracle_adjoint_s_1core_est_64": t_or / 2 * 64,
             "fd_check": "against FP64 central differences in tests/test_gpu_grad.py (<= 1e-6 relative)"}
 
 

@@ -437,6 +437,40 @@ rbd_status rbd_grad(const void* X, rbd_dtype xt, int64_t m, int64_t n, int64_t l
                     double w_rec, double w_proj,
                     double* G, int64_t ldg, double* loss, void* stream);
 
+/*
+ * rbd_grad_batched -- rbd_grad for many independent instances at once (the differentiation form
+ * of a batch of matrices): each of rbd_grad's kernels is launched once for the whole batch, the
+ * out-of-sample map C = Y' Xo once per instance.  Each instance's loss and gradient are those of
+ * rbd_grad on it, to the bit (the same kernels and summation order).
+ *
+ *  items   [in]  host array of `count` descriptors, fields as rbd_grad's arguments; every G is
+ *                non-NULL (gradients) or every G is NULL (losses only).
+ *  count   [in]  1 .. 65535.
+ *  xt, w_rec, w_proj, stream  as for rbd_grad (one storage type and one pair of weights for the
+ *                batch).  Stream-ordered; one stream-ordered workspace allocation, freed before
+ *                return; does not synchronise.
+ *  Errors: those of rbd_grad for any instance; RBD_EINVAL for count out of range or a mix of NULL
+ *  and non-NULL G.
+ */
+typedef struct rbd_grad_item {
+    const void* X;        /* device, m x n, ldx >= m */
+    int64_t m, n, ldx;
+    const double* Y;      /* device FP64, m x d, ldy >= m */
+    int64_t ldy;
+    const double* T;      /* device FP64, d x n, ldt >= d */
+    int64_t ldt;
+    const int64_t* pivots;/* device, d entries */
+    int64_t d;            /* 0 <= d <= min(m, n, 256) */
+    const void* Xo;       /* device, m x k, ldxo >= m; may be NULL when k = 0 */
+    int64_t k, ldxo;
+    double* G;            /* device FP64, m x n, ldg >= m; or NULL */
+    int64_t ldg;
+    double* loss;         /* device, one double */
+} rbd_grad_item;
+
+rbd_status rbd_grad_batched(const rbd_grad_item* items, int64_t count, rbd_dtype xt,
+                            double w_rec, double w_proj, void* stream);
+
 /* Per-kernel timing of the most recent rbd_compress call on this host thread, taken with
    CUDA events recorded on the call's stream around each launch when profiling is enabled
    (rbd_set_profiling(1)).  Times are in milliseconds. */

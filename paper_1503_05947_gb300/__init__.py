@@ -15,6 +15,7 @@ from .rbd import (  # noqa: F401
     compress_resume,
     compress_rows,
     grad,
+    grad_batched,
     get_profile,
     load,
     project,

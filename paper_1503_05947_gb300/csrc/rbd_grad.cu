@@ -8,7 +8,8 @@
 // and dP_A = (I - P_A) dA A^+ + (A^+)' dA' (I - P_A), A^+ = R^-1 Y', the gradient is
 //     G = 2 w_rec E                                             E = X - Y T
 //     G(:, P) += [-2 w_rec E T' + 2 w_proj (Xo - Y C) C'] R^-T, C = Y' Xo.
-// Kernels (one stream, in order):
+// Kernels (one stream, in order; rbd_grad_batched launches each once for a whole batch, the CTA's
+// blockIdx.y picking the instance, and C = Y' Xo once per instance):
 //   grad_pass_kernel   one pass over X by 32-row blocks: E = X - Y T (float-float), G = 2 w_rec E,
 //                      M1 = E T' (m x d, float-float, from E held in shared memory), ||E||^2
 //   project_kernel     C = Y' Xo (rbd_project's kernel)
@@ -20,6 +21,7 @@
 // results, so they run as float-float on the FP32 pipes (FP64 is 1/64 rate on GB300; BF16 tensor
 // products would lose the accuracy).
 #include <algorithm>
+#include <vector>
 
 #include "../../include/rbd.h"
 #include "rbd_device.cuh"
@@ -68,7 +70,7 @@ size_t grad_pass_smem(int64_t d) {
 }
 
 template <bool WITH_G>
-__global__ void __launch_bounds__(kGThreads) grad_pass_kernel(GradParams p) {
+__device__ __forceinline__ void grad_pass_body(const GradParams& p) {
     extern __shared__ __align__(16) float gsm[];
     const int d = (int)p.d;
     float* Ysh = gsm;                       // [d][kGR]
@@ -151,8 +153,21 @@ __global__ void __launch_bounds__(kGThreads) grad_pass_kernel(GradParams p) {
     if (tid == 0) p.epart[blockIdx.x] = red[0];
 }
 
+template <bool WITH_G>
+__global__ void __launch_bounds__(kGThreads) grad_pass_kernel(GradParams p) {
+    grad_pass_body<WITH_G>(p);
+}
+
+// Batched: instance blockIdx.y; the grid is as wide as the tallest instance needs.
+template <bool WITH_G>
+__global__ void __launch_bounds__(kGThreads) grad_pass_batched(const GradParams* ps) {
+    const GradParams& p = ps[blockIdx.y];
+    if ((int64_t)blockIdx.x * kGR >= p.m) return;
+    grad_pass_body<WITH_G>(p);
+}
+
 // CC = C C' (d x d) and ||C||^2, one CTA, float-float over k.
-__global__ void __launch_bounds__(kGThreads) grad_small_kernel(GradParams p) {
+__device__ __forceinline__ void grad_small_body(const GradParams& p) {
     __shared__ double red[kGThreads];
     const int tid = threadIdx.x;
     const int64_t d = p.d, k = p.k;
@@ -178,13 +193,25 @@ __global__ void __launch_bounds__(kGThreads) grad_small_kernel(GradParams p) {
     if (tid == 0) *p.c2 = red[0];
 }
 
+__global__ void __launch_bounds__(kGThreads) grad_small_kernel(GradParams p) { grad_small_body(p); }
+
+// Batched: one CTA per instance; instances without both Y and Xo get CC = 0.
+__global__ void __launch_bounds__(kGThreads) grad_small_batched(const GradParams* ps) {
+    const GradParams& p = ps[blockIdx.y];
+    if (p.d > 0 && p.k > 0) {
+        grad_small_body(p);
+    } else {
+        for (int64_t o = threadIdx.x; o < p.d * p.d; o += kGThreads) p.CC[o] = 0.0;
+    }
+}
+
 // Pivot columns: Z = -2 w_rec M1 + 2 w_proj (Xo C' - Y CC), W = Z R^-T, G(:, P(l)) += W(:, l).
 // Shared memory: Z [d][kGR] doubles, Xo tile [kGCT][kGR] and C tile [d][kGCT] (split floats).
 size_t grad_pivot_smem(int64_t d) {
     return (size_t)kGR * d * 8 + (size_t)2 * kGR * kGCT * 4 + (size_t)2 * d * kGCT * 4;
 }
 
-__global__ void __launch_bounds__(kGThreads) grad_pivot_kernel(GradParams p) {
+__device__ __forceinline__ void grad_pivot_body(const GradParams& p) {
     extern __shared__ __align__(16) unsigned char psm[];
     const int d = (int)p.d;
     double* Z = reinterpret_cast<double*>(psm);         // [d][kGR]
@@ -264,11 +291,29 @@ __global__ void __launch_bounds__(kGThreads) grad_pivot_kernel(GradParams p) {
     }
 }
 
+__global__ void __launch_bounds__(kGThreads) grad_pivot_kernel(GradParams p) { grad_pivot_body(p); }
+
+__global__ void __launch_bounds__(kGThreads) grad_pivot_batched(const GradParams* ps) {
+    const GradParams& p = ps[blockIdx.y];
+    if ((int64_t)blockIdx.x * kGR >= p.m || p.d == 0 || !p.G) return;
+    grad_pivot_body(p);
+}
+
+__device__ __forceinline__ void grad_loss_body(const GradParams& p, int64_t nblocks) {
+    double e2 = 0.0;
+    for (int64_t b = 0; b < nblocks; ++b) e2 += p.epart[b];
+    *p.loss = p.w_rec * e2 + p.w_proj * (p.k > 0 && p.d > 0 ? *p.c2 : 0.0);
+}
+
 __global__ void grad_loss_kernel(GradParams p, int nblocks) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double e2 = 0.0;
-    for (int b = 0; b < nblocks; ++b) e2 += p.epart[b];
-    *p.loss = p.w_rec * e2 + p.w_proj * (p.k > 0 && p.d > 0 ? *p.c2 : 0.0);
+    grad_loss_body(p, nblocks);
+}
+
+// Batched: thread i sums instance i's row-block partials (the same order as grad_loss_kernel).
+__global__ void grad_loss_batched(const GradParams* ps, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) grad_loss_body(ps[i], ceil_div(ps[i].m, (int64_t)kGR));
 }
 
 rbd_status map_cuda_status(cudaError_t e) {
@@ -366,6 +411,118 @@ extern "C" rbd_status rbd_grad(const void* X, rbd_dtype xt, int64_t m, int64_t n
     }
     if (ce == cudaSuccess) {
         grad_loss_kernel<<<1, 32, 0, st>>>(p, (int)nb);
+        ce = cudaGetLastError();
+    }
+    cudaError_t fe = cudaFreeAsync(ws, st);
+    if (ce == cudaSuccess) ce = fe;
+    if (ce != cudaSuccess) cudaGetLastError();
+    return map_cuda_status(ce);
+}
+
+extern "C" rbd_status rbd_grad_batched(const rbd_grad_item* items, int64_t count, rbd_dtype xt, double w_rec,
+                                       double w_proj, void* stream) {
+    if (!items || count < 1 || count > 65535) return RBD_EINVAL;
+    if (xt != RBD_F64 && xt != RBD_F32 && xt != RBD_BF16) return RBD_EINVAL;
+    if (!(w_rec == w_rec) || !(w_proj == w_proj)) return RBD_EINVAL;
+    const bool with_g = items[0].G != nullptr;
+    int64_t max_nb = 1, max_d = 1;
+    size_t total = ((size_t)count * sizeof(GradParams) + 255) & ~(size_t)255;
+    std::vector<size_t> off((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        const rbd_grad_item& it = items[i];
+        if (!it.X || !it.loss || it.m < 1 || it.n < 1 || it.ldx < it.m || it.d < 0 || it.d > it.m || it.d > it.n ||
+            it.k < 0)
+            return RBD_EINVAL;
+        if (it.d > 0 && (!it.Y || !it.T || !it.pivots || it.ldy < it.m || it.ldt < it.d)) return RBD_EINVAL;
+        if (it.k > 0 && (!it.Xo || it.ldxo < it.m)) return RBD_EINVAL;
+        if ((it.G != nullptr) != with_g || (it.G && it.ldg < it.m)) return RBD_EINVAL;
+        if (it.d > kGradMaxD) return RBD_EUNSUPPORTED;
+        const int64_t nb = ceil_div(it.m, (int64_t)kGR);
+        if (nb > (int64_t)1 << 31) return RBD_EUNSUPPORTED;
+        max_nb = std::max(max_nb, nb);
+        max_d = std::max(max_d, it.d);
+        const int64_t dd = std::max<int64_t>(it.d, 1), kk = std::max<int64_t>(it.k, 1);
+        off[(size_t)i] = total;
+        total += ((size_t)it.m * dd * 8 + (size_t)dd * kk * 8 + (size_t)dd * dd * 8 + (size_t)nb * 8 + 64 + 255) &
+                 ~(size_t)255;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    void* ws = nullptr;
+    cudaError_t ce = cudaMallocAsync(&ws, total, st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return RBD_ENOMEM;
+    }
+    unsigned char* w = (unsigned char*)ws;
+    std::vector<GradParams> hp((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        const rbd_grad_item& it = items[i];
+        GradParams& p = hp[(size_t)i];
+        const int64_t dd = std::max<int64_t>(it.d, 1), kk = std::max<int64_t>(it.k, 1);
+        const int64_t nb = ceil_div(it.m, (int64_t)kGR);
+        unsigned char* b = w + off[(size_t)i];
+        p.X = it.X;
+        p.xt = (int)xt;
+        p.m = it.m;
+        p.n = it.n;
+        p.ldx = it.ldx;
+        p.Y = it.Y;
+        p.ldy = it.ldy;
+        p.T = it.T;
+        p.ldt = it.ldt;
+        p.piv = it.pivots;
+        p.d = it.d;
+        p.Xo = it.Xo;
+        p.k = it.k;
+        p.ldxo = it.ldxo;
+        p.w_rec = w_rec;
+        p.w_proj = w_proj;
+        p.G = it.G;
+        p.ldg = it.ldg;
+        p.M1 = (double*)b;
+        p.C = (double*)(b + (size_t)it.m * dd * 8);
+        p.CC = (double*)(b + (size_t)it.m * dd * 8 + (size_t)dd * kk * 8);
+        p.epart = (double*)(b + (size_t)it.m * dd * 8 + (size_t)dd * kk * 8 + (size_t)dd * dd * 8);
+        p.c2 = (double*)(b + (size_t)it.m * dd * 8 + (size_t)dd * kk * 8 + (size_t)dd * dd * 8 + (size_t)nb * 8);
+        p.loss = it.loss;
+    }
+    const GradParams* dp = (const GradParams*)w;
+    // a pageable source: the call returns once the table is staged, so hp may go out of scope
+    ce = cudaMemcpyAsync(w, hp.data(), (size_t)count * sizeof(GradParams), cudaMemcpyHostToDevice, st);
+    const size_t sm_pass = grad_pass_smem(max_d), sm_piv = grad_pivot_smem(max_d);
+    const dim3 grid_rows((unsigned)max_nb, (unsigned)count);
+    if (ce == cudaSuccess) {
+        if (with_g) {
+            ce = cudaFuncSetAttribute(grad_pass_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_pass);
+            if (ce == cudaSuccess)
+                ce = cudaFuncSetAttribute(grad_pivot_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_piv);
+            if (ce == cudaSuccess) {
+                grad_pass_batched<true><<<grid_rows, kGThreads, sm_pass, st>>>(dp);
+                ce = cudaGetLastError();
+            }
+        } else {
+            ce = cudaFuncSetAttribute(grad_pass_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_pass);
+            if (ce == cudaSuccess) {
+                grad_pass_batched<false><<<grid_rows, kGThreads, sm_pass, st>>>(dp);
+                ce = cudaGetLastError();
+            }
+        }
+    }
+    for (int64_t i = 0; i < count && ce == cudaSuccess; ++i) {
+        const rbd_grad_item& it = items[i];
+        if (it.d > 0 && it.k > 0)
+            ce = launch_project(it.Y, it.m, it.d, it.ldy, it.Xo, (int)xt, it.k, it.ldxo, hp[(size_t)i].C, it.d, st);
+    }
+    if (ce == cudaSuccess) {
+        grad_small_batched<<<dim3(1, (unsigned)count), kGThreads, 0, st>>>(dp);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess && with_g) {
+        grad_pivot_batched<<<grid_rows, kGThreads, sm_piv, st>>>(dp);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) {
+        grad_loss_batched<<<(unsigned)ceil_div(count, 128), 128, 0, st>>>(dp, count);
         ce = cudaGetLastError();
     }
     cudaError_t fe = cudaFreeAsync(ws, st);

@@ -51,6 +51,12 @@ class _BatchConfig(ctypes.Structure):
                 ("stages", ctypes.c_int32)]
 
 
+class _GradItem(ctypes.Structure):
+    _fields_ = [("X", _PTR), ("m", _I64), ("n", _I64), ("ldx", _I64), ("Y", _PTR), ("ldy", _I64), ("T", _PTR),
+                ("ldt", _I64), ("pivots", _PTR), ("d", _I64), ("Xo", _PTR), ("k", _I64), ("ldxo", _I64), ("G", _PTR),
+                ("ldg", _I64), ("loss", _PTR)]
+
+
 class _Instance(ctypes.Structure):
     _fields_ = [("X", _PTR), ("m", _I64), ("n", _I64), ("ldx", _I64), ("tol", _DBL), ("mode", ctypes.c_int32),
                 ("d_hint", ctypes.c_int32), ("d_max", _I64), ("start", _I64), ("Y", _PTR), ("ldy", _I64),
@@ -104,6 +110,8 @@ def load():
     lib.rbd_grad.restype = ctypes.c_int
     lib.rbd_grad.argtypes = [_PTR, ctypes.c_int, _I64, _I64, _I64, _PTR, _I64, _PTR, _I64, _PTR, _I64, _PTR, _I64,
                              _I64, _DBL, _DBL, _PTR, _I64, _PTR, _PTR]
+    lib.rbd_grad_batched.restype = ctypes.c_int
+    lib.rbd_grad_batched.argtypes = [ctypes.POINTER(_GradItem), _I64, ctypes.c_int, _DBL, _DBL, _PTR]
     lib.rbd_batch_workspace_bytes.restype = ctypes.c_size_t
     lib.rbd_batch_workspace_bytes.argtypes = [ctypes.POINTER(_Instance), _I64, ctypes.c_int]
     lib.rbd_batch_plan_create.restype = ctypes.c_int
@@ -418,6 +426,53 @@ def grad(X: torch.Tensor, Y: torch.Tensor, T: torch.Tensor, pivots: torch.Tensor
                           loss.data_ptr(), _stream_ptr(dev))
     _check(st, "rbd_grad")
     return G, loss
+
+
+def grad_batched(items, w_rec: float = 1.0, w_proj: float = 1.0, need_grad: bool = True):
+    """rbd_grad_batched: ``grad`` for a list of instances in one set of launches.  Each item is a dict
+    with X, Y, T, pivots and optionally Xo (all CUDA tensors on one device, X and Xo of one storage
+    type); returns a list of (G or None, loss) as ``grad`` would for each item."""
+    lib = load()
+    if not items:
+        return []
+    dev = items[0]["X"].device
+    xdt = items[0]["X"].dtype
+    arr = (_GradItem * len(items))()
+    keep, outs = [], []
+    for i, it in enumerate(items):
+        X = it["X"]
+        if not X.is_cuda or X.dtype != xdt or X.device != dev:
+            raise ValueError("every X must be a CUDA tensor of one dtype on one device")
+        m, n = X.shape
+        ldx = _colmajor(X, "X")
+        d = int(it["pivots"].numel())
+        Y, T = it["Y"], it["T"]
+        if d > 0:
+            if Y.dtype != torch.float64 or T.dtype != torch.float64:
+                raise ValueError("Y and T must be float64")
+            ldy, ldt = _colmajor(Y, "Y"), _colmajor(T, "T")
+            piv = it["pivots"].to(device=dev, dtype=torch.int64).contiguous()
+        else:
+            ldy, ldt, piv = m, 1, None
+        Xo = it.get("Xo")
+        k, ldxo, xo_ptr = 0, m, None
+        if Xo is not None and Xo.numel() > 0:
+            if Xo.dtype != xdt:
+                raise ValueError("Xo must have the dtype of X")
+            if Xo.dim() == 1:
+                Xo = Xo[:, None]
+            k, ldxo, xo_ptr = Xo.shape[1], _colmajor(Xo, "Xo"), Xo.data_ptr()
+        G = colmajor_empty(m, n, torch.float64, dev) if need_grad else None
+        loss = torch.empty((), dtype=torch.float64, device=dev)
+        keep += [piv, Xo]
+        outs.append((G, loss))
+        arr[i] = _GradItem(X.data_ptr(), m, n, ldx, Y.data_ptr() if d > 0 else None, ldy,
+                           T.data_ptr() if d > 0 else None, ldt, piv.data_ptr() if d > 0 else None, d, xo_ptr, k, ldxo,
+                           G.data_ptr() if G is not None else None, m, loss.data_ptr())
+    with torch.cuda.device(dev):
+        st = lib.rbd_grad_batched(arr, len(items), DTYPES[xdt], float(w_rec), float(w_proj), _stream_ptr(dev))
+    _check(st, "rbd_grad_batched")
+    return outs
 
 
 def reconstruct(Y: torch.Tensor, T: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:

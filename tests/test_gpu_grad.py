@@ -100,3 +100,66 @@ def test_differentiation_workload_batch_matches_oracle(rbd, oracle_mod):
         assert abs(lg.item() - lref) <= 1e-12 * lref, i
         # the autograd gradient is the adjoint cast to the input dtype
         assert np.abs(to_numpy(Xt.grad) - Gn).max() <= 1e-6 * np.abs(Gn).max()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_grad_batched_equals_one_by_one(rbd, dtype):
+    """rbd_grad_batched gives each instance rbd_grad's loss and gradient bit for bit, on a ragged
+    batch: row counts not multiples of the 32-row block, an instance with d = 0, one without
+    out-of-sample data, one with a single out-of-sample vector; and the loss-only form."""
+    shapes = [(100, 37, 8, 16), (256, 64, 0, 8), (777, 333, 40, 0), (33, 20, 5, 1), (1024, 512, 32, 256)]
+    items = []
+    for i, (m, n, d, k) in enumerate(shapes):
+        X = to_device(np.asfortranarray(gen.lowrank_haar(m, n, np.exp(-0.1 * np.arange(min(m, n))), seed=300 + i)),
+                      dtype)
+        Xo = to_device(np.asfortranarray(gen.out_of_sample(m, k, seed=400 + i)), dtype) if k else None
+        r = rbd.compress(X, 0.0, max(d, 1))
+        items.append({"X": X, "Y": r.Y[:, :d], "T": r.T[:d], "pivots": r.pivots[:d], "Xo": Xo})
+    for need in (True, False):
+        outs = rbd.grad_batched(items, 1.25, 0.75, need_grad=need)
+        for it, (G, loss) in zip(items, outs):
+            G1, l1 = rbd.grad(it["X"], it["Y"], it["T"], it["pivots"], it["Xo"], 1.25, 0.75, need_grad=need)
+            assert torch.equal(loss, l1)
+            assert (G is None and G1 is None) if not need else torch.equal(G, G1)
+
+
+def test_grad_batched_differentiation_workload(rbd, oracle_mod):
+    """The differentiation workload as a batch: the 64 compressions in one batched launch (tol 0,
+    d = 32), the 64 adjoints in one rbd_grad_batched call; the pivots equal rbd_compress's, and
+    sampled gradients match the oracle's adjoint on the same factors to 1e-10 of max |G|."""
+    host = [c5_instance(i) for i in range(64)]
+    items = [{"X": to_device(X, torch.float32), "tol": 0.0, "d_max": 32} for X, _ in host]
+    plan = rbd.BatchPlan(items)
+    plan.run()
+    res = plan.results()
+    gi = []
+    for i, (it, r) in enumerate(zip(items, res)):
+        assert r["d"] == 32 and r["status"] == 0, i
+        c = plan.compressed(i, r)
+        gi.append({"X": it["X"], "Y": c.Y, "T": c.T, "pivots": c.pivots, "Xo": to_device(host[i][1], torch.float32)})
+    outs = rbd.grad_batched(gi)
+    for i in (0, 21, 63):
+        one = rbd.compress(items[i]["X"], 0.0, 32)
+        assert torch.equal(one.pivots, gi[i]["pivots"]), i
+        X, Xo = host[i]
+        Gref, lref = oracle_mod.grad(X.astype(np.float64), to_numpy(gi[i]["Y"]), to_numpy(gi[i]["T"]),
+                                     gi[i]["pivots"].cpu().numpy(), Xo.astype(np.float64), 1.0, 1.0)
+        G, loss = outs[i]
+        assert np.abs(to_numpy(G) - Gref).max() <= 1e-10 * np.abs(Gref).max(), i
+        assert abs(loss.item() - lref) <= 1e-12 * lref, i
+
+
+def test_grad_batched_rejects_mixed_outputs(rbd):
+    X = to_device(np.asfortranarray(gen.lowrank_haar(64, 32, np.exp(-0.3 * np.arange(32)), seed=5)))
+    r = rbd.compress(X, 0.0, 4)
+    it = {"X": X, "Y": r.Y, "T": r.T, "pivots": r.pivots}
+    lib = rbd.load()
+    from paper_1503_05947_gb300.rbd import _GradItem, _stream_ptr
+    G = torch.empty(32, 64, dtype=torch.float64, device=X.device).t()
+    loss = torch.empty(2, dtype=torch.float64, device=X.device)
+    arr = (_GradItem * 2)()
+    for i, g in enumerate((G.data_ptr(), None)):
+        arr[i] = _GradItem(X.data_ptr(), 64, 32, 64, it["Y"].data_ptr(), 64, it["T"].data_ptr(), 4,
+                           it["pivots"].data_ptr(), 4, None, 0, 64, g, 64, loss[i:].data_ptr())
+    assert lib.rbd_grad_batched(arr, 2, 0, 1.0, 1.0, _stream_ptr(X.device)) == 1  # RBD_EINVAL
+    assert lib.rbd_grad_batched(arr, 0, 0, 1.0, 1.0, _stream_ptr(X.device)) == 1
