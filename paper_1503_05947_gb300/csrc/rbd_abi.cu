@@ -698,7 +698,7 @@ rbd_status rbd_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy, c
     if (!Xr || ldxr < m) return RBD_EINVAL;
     if (d > 0 && (!Y || !T || ldy < m || ldt < d)) return RBD_EINVAL;
     if (m > (int64_t(1) << 40) || n > (int64_t(1) << 31) || d > (int64_t(1) << 30)) return RBD_EUNSUPPORTED;
-    if (ceil_div(m, (int64_t)32) > (int64_t(1) << 31) - 1) return RBD_EUNSUPPORTED;
+    if (ceil_div(m, (int64_t)64) > (int64_t(1) << 31) - 1) return RBD_EUNSUPPORTED;
     return map_cuda(launch_reconstruct(Y, m, d, ldy, T, n, ldt, Xr, ldxr, (cudaStream_t)stream));
 }
 

@@ -135,9 +135,11 @@ namespace rbd {
 
 // ---------------------------------------------------------------------------------------------
 // Uncompress (Section 3.1): Xr = Y T, column j of the approximation = Y T(:, j) (Section 3.3:
-// m d per column).  Each CTA owns a 32 x 32 tile of Xr and walks the d bases in chunks of 32,
-// staged in shared memory as float-float; thread (row = tid % 32, col = tid / 32 + 8 q)
-// accumulates over the bases in order: deterministic, FP64-grade on the FP32 pipes.
+// m d per column).  Each CTA owns a 64 x 64 tile of Xr and walks the d bases in chunks of 32,
+// staged in shared memory as float-float; thread (tx = tid % 16, ty = tid / 16) accumulates the
+// 4 x 4 outputs of rows 4 tx .. 4 tx + 3 and columns 4 ty .. 4 ty + 3 over the bases in order:
+// deterministic, FP64-grade on the FP32 pipes.  Per basis a thread reads its 4 rows of Y as two
+// 16-byte loads and its 4 columns of T as 8 broadcast words, for 16 float-float products.
 // ---------------------------------------------------------------------------------------------
 struct ReconParams {
     const double* Y;
@@ -148,43 +150,65 @@ struct ReconParams {
     int64_t ldxr;
 };
 
+constexpr int kRT = 64;  // tile edge (rows and columns of Xr)
+constexpr int kRL = 32;  // bases per staged chunk
+
 __global__ void __launch_bounds__(256) reconstruct_kernel(ReconParams p) {
-    __shared__ float yh[kPT][kPT], yl[kPT][kPT];           // [basis][row]
-    __shared__ float th[kPT][kPT + 1], tl[kPT][kPT + 1];   // [col][basis]
+    __shared__ __align__(16) float yh[kRL][kRT];  // [basis][row]
+    __shared__ __align__(16) float yl[kRL][kRT];
+    __shared__ float th[kRT][kRL + 1], tl[kRT][kRL + 1];         // [col][basis]
     const int tid = threadIdx.x;
-    const int row = tid % kPT, cq = tid / kPT;
-    const int64_t r0 = (int64_t)blockIdx.x * kPT, j0 = (int64_t)blockIdx.y * kPT;
-    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t l0 = 0; l0 < p.d; l0 += kPT) {
-        for (int idx = tid; idx < kPT * kPT; idx += 256) {
-            const int a = idx % kPT, b = idx / kPT;
-            // Y(r0 + a, l0 + b) and T(l0 + a, j0 + b)
-            double y = 0.0, t = 0.0;
-            if (r0 + a < p.m && l0 + b < p.d) y = p.Y[(l0 + b) * p.ldy + r0 + a];
-            if (l0 + a < p.d && j0 + b < p.n) t = p.T[(j0 + b) * p.ldt + l0 + a];
-            // integer splits: FP64 arithmetic here would cost as much as the products below
-            float hi, lo;
-            split_f64_fast(y, hi, lo);
-            yh[b][a] = hi;
-            yl[b][a] = lo;
-            split_f64_fast(t, hi, lo);
-            th[b][a] = hi;
-            tl[b][a] = lo;
-        }
-        __syncthreads();
-        const int lc = (int)min((int64_t)kPT, p.d - l0);
-        for (int l = 0; l < lc; ++l) {
-            const float ah = yh[l][row], al = yl[l][row];
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t r0 = (int64_t)blockIdx.x * kRT;
+    // column tiles blockIdx.y, blockIdx.y + gridDim.y, ... (the grid's y extent is capped)
+    for (int64_t j0 = (int64_t)blockIdx.y * kRT; j0 < p.n; j0 += (int64_t)gridDim.y * kRT) {
+        float s[4][4], c[4][4];  // [column][row]
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ff_mac2(s[q], c[q], ah, al, th[cq + 8 * q][l], tl[cq + 8 * q][l]);
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s[q][u] = c[q][u] = 0.f;
+        for (int64_t l0 = 0; l0 < p.d; l0 += kRL) {
+            for (int idx = tid; idx < kRT * kRL; idx += 256) {
+                // Y(r0 + a, l0 + b): rows fastest; T(l0 + a2, j0 + b2): bases fastest (both coalesced)
+                const int a = idx % kRT, b = idx / kRT;
+                const int a2 = idx % kRL, b2 = idx / kRL;
+                double y = 0.0, t = 0.0;
+                if (r0 + a < p.m && l0 + b < p.d) y = p.Y[(l0 + b) * p.ldy + r0 + a];
+                if (l0 + a2 < p.d && j0 + b2 < p.n) t = p.T[(j0 + b2) * p.ldt + l0 + a2];
+                // integer splits: FP64 arithmetic here would cost as much as the products below
+                float hi, lo;
+                split_f64_fast(y, hi, lo);
+                yh[b][a] = hi;
+                yl[b][a] = lo;
+                split_f64_fast(t, hi, lo);
+                th[b2][a2] = hi;
+                tl[b2][a2] = lo;
+            }
+            __syncthreads();
+            const int lc = (int)min((int64_t)kRL, p.d - l0);
+            for (int l = 0; l < lc; ++l) {
+                const float4 ah = *reinterpret_cast<const float4*>(&yh[l][4 * tx]);
+                const float4 al = *reinterpret_cast<const float4*>(&yl[l][4 * tx]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float bh = th[4 * ty + q][l], bl = tl[4 * ty + q][l];
+                    ff_mac2(s[q][0], c[q][0], ah.x, al.x, bh, bl);
+                    ff_mac2(s[q][1], c[q][1], ah.y, al.y, bh, bl);
+                    ff_mac2(s[q][2], c[q][2], ah.z, al.z, bh, bl);
+                    ff_mac2(s[q][3], c[q][3], ah.w, al.w, bh, bl);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-    }
-    if (r0 + row < p.m) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int64_t j = j0 + cq + 8 * q;
-            if (j < p.n) p.Xr[j * p.ldxr + r0 + row] = ff_to_double(s[q], c[q]);
+            const int64_t j = j0 + 4 * ty + q;
+            if (j >= p.n) continue;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t r = r0 + 4 * tx + u;
+                if (r < p.m) p.Xr[j * p.ldxr + r] = ff_to_double(s[q][u], c[q][u]);
+            }
         }
     }
 }
@@ -192,7 +216,7 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(ReconParams p) {
 cudaError_t launch_reconstruct(const double* Y, int64_t m, int64_t d, int64_t ldy, const double* T, int64_t n,
                                int64_t ldt, double* Xr, int64_t ldxr, cudaStream_t st) {
     ReconParams p{Y, m, d, ldy, T, n, ldt, Xr, ldxr};
-    dim3 grid((unsigned)ceil_div(m, (int64_t)kPT), (unsigned)ceil_div(n, (int64_t)kPT));
+    dim3 grid((unsigned)ceil_div(m, (int64_t)kRT), (unsigned)std::min<int64_t>(ceil_div(n, (int64_t)kRT), 65535));
     reconstruct_kernel<<<grid, 256, 0, st>>>(p);
     return cudaGetLastError();
 }

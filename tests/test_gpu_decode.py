@@ -61,3 +61,17 @@ def test_reconstruct_degenerate(rbd):
     Y1 = torch.ones((3, 50), dtype=torch.float64, device="cuda").t()
     T0 = torch.zeros((3, 0), dtype=torch.float64, device="cuda")
     assert rbd.reconstruct(Y1, T0).shape == (50, 0)
+
+
+def test_reconstruct_wide_grid(rbd):
+    """More column tiles than a grid's y extent holds (n > 65535 x 64): the kernel walks the
+    remaining tiles; sampled columns against numpy."""
+    m, d, n = 3, 2, 65535 * 64 + 100
+    g = torch.Generator(device="cuda").manual_seed(11)
+    Y = torch.randn((d, m), dtype=torch.float64, device="cuda", generator=g).t()
+    T = torch.randn((n, d), dtype=torch.float64, device="cuda", generator=g).t()
+    out = rbd.reconstruct(Y, T)
+    cols = torch.tensor([0, 1, 65535 * 64 - 1, 65535 * 64, n - 1], device="cuda")
+    ref = (to_numpy(Y) @ to_numpy(T[:, cols]))
+    assert np.abs(to_numpy(out[:, cols]) - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert torch.isfinite(out).all()
