@@ -198,15 +198,16 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
     float* ring = reinterpret_cast<float*>(bsm);                               // kBRingBytes
     uint64_t* full = reinterpret_cast<uint64_t*>(bsm + kBRingBytes);           // SMAX
     uint64_t* empty = full + SMAX;                                             // SMAX
-    uint64_t* ybar = empty + SMAX;                                             // kBNB
-    float* vh = reinterpret_cast<float*>(ybar + kBNB);                         // kBMaxRows
+    uint64_t* ybar = empty + SMAX;                                             // kBNB: chunk landed
+    uint64_t* yempty = ybar + kBNB;                                            // kBNB: chunk consumed
+    float* vh = reinterpret_cast<float*>(yempty + kBNB);                       // kBMaxRows
     float* vl = vh + kBMaxRows;                                                // kBMaxRows
     double* hacc = reinterpret_cast<double*>(vl + kBMaxRows);                  // kBMaxD
     float* cst_h = reinterpret_cast<float*>(hacc + kBMaxD);                    // kBMaxD: coefficients (hi)
     float* cst_l = cst_h + kBMaxD;                                             // kBMaxD: (lo)
-    float* wps = cst_l + kBMaxD;                                               // kBNW x kBMaxLC (ff hi)
-    float* wpc = wps + kBNW * kBMaxLC;                                         // (ff lo)
-    double* red = reinterpret_cast<double*>(wpc + kBNW * kBMaxLC);             // 4 kBNW + 16
+    float* wps = cst_l + kBMaxD;                                               // kBNW x kBMaxD (ff hi)
+    float* wpc = wps + kBNW * kBMaxD;                                          // (ff lo)
+    double* red = reinterpret_cast<double*>(wpc + kBNW * kBMaxD);              // 4 kBNW + 16
     int64_t* redj = reinterpret_cast<int64_t*>(red + 2 * kBNW);
     double* bc = red + 4 * kBNW;                                               // broadcasts
     int* flag = reinterpret_cast<int*>(bc + 8);
@@ -219,7 +220,10 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kBNW);
         }
-        for (int bq = 0; bq < kBNB; ++bq) mbar_init(&ybar[bq], 1);
+        for (int bq = 0; bq < kBNB; ++bq) {
+            mbar_init(&ybar[bq], 1);
+            mbar_init(&yempty[bq], kBNW);
+        }
         fence_mbar_init();
     }
     __syncthreads();
@@ -306,24 +310,28 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
         double fro_prev = x_fro, err_last = 0.0;
         int32_t stop = (st0 != ST_OK) ? STOP_BREAK : STOP_NONE;
         int64_t k = 0;
-        // Y chunk geometry: the ring as kBNB buffers, both planes per chunk (few large chunks: each
-        // chunk costs two barriers, more than its copy latency)
+        // Y chunk geometry: the ring as kBNB buffers, both planes per chunk
         const int64_t buf_f = kBRingBytes / 4 / kBNB;  // floats per buffer
         const int LC = (int)max((int64_t)1, min((int64_t)kBMaxLC, buf_f / (2 * rb)));
 
         // streams columns [0, k) of this member's Y block in chunks through the ring buffers, up
         // to kBNB in flight (consumer threads); stage(l, hi, lo) gives the coefficient of column l
         // (all k staged once, before the first chunk), body(yh, yl, ch, cl, l0, lc) runs on the
-        // chunk, post(l0, lc) after the barrier that closes it.  Every barrier is reached by all
-        // consumer threads whatever their waits returned.
-        auto ystream = [&](auto&& stage, auto&& body, auto&& post) {
+        // chunk.  No barrier per chunk: each consumer warp marks a chunk consumed on the buffer's
+        // yempty barrier, and thread 0 waits there (for the buffer's previous chunk) before it
+        // refills a buffer.  Every consumer warp arrives whatever its waits returned.
+        auto ystream = [&](auto&& stage, auto&& body) {
             const int64_t nch = ceil_div(k, (int64_t)LC);
             auto issue = [&](int64_t c) {
-                const int bf = (int)((ycount + (uint32_t)c) % (uint32_t)kBNB);
+                const uint32_t gc = ycount + (uint32_t)c;
+                const int bf = (int)(gc % (uint32_t)kBNB);
+                if (gc >= (uint32_t)kBNB && ok && !mbar_wait(&yempty[bf], (gc / (uint32_t)kBNB - 1u) & 1u, bp.wait_ns))
+                    ok = false;
+                if (!ok) return;
                 const int64_t l0 = c * LC;
                 const int lc = (int)min((int64_t)LC, k - l0);
                 const uint32_t bytes = (uint32_t)(lc * rb * 4);
-                yiss = max(yiss, ycount + (uint32_t)c + 1u);
+                yiss = max(yiss, gc + 1u);
                 mbar_arrive_expect_tx(&ybar[bf], 2u * bytes);
                 bulk_g2s(ring + bf * buf_f, ysb + l0 * rb, bytes, &ybar[bf], pol_y);
                 bulk_g2s(ring + bf * buf_f + (int64_t)LC * rb, ysb + (dmax + l0) * rb, bytes, &ybar[bf], pol_y);
@@ -331,9 +339,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
             if (tid == 0)
                 for (int64_t c = 0; c < min(nch, (int64_t)kBNB); ++c) issue(c);
             for (int64_t l = tid; l < k; l += kBNCONS) stage(l, cst_h[l], cst_l[l]);
+            named_bar(1, kBNCONS);  // coefficients visible
             for (int64_t c = 0; c < nch; ++c) {
-                // coefficients visible (first chunk); post of chunk c - 1 done before body reuses its scratch
-                named_bar(1, kBNCONS);
                 const int bf = (int)((ycount + (uint32_t)c) % (uint32_t)kBNB);
                 const int64_t l0 = c * LC;
                 const int lc = (int)min((int64_t)LC, k - l0);
@@ -343,13 +350,12 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                     else ok = false;
                 }
                 if (ok) body(ring + bf * buf_f, ring + bf * buf_f + (int64_t)LC * rb, cst_h + l0, cst_l + l0, l0, lc);
-                named_bar(1, kBNCONS);  // chunk c consumed: its buffer may be refilled
-                post(l0, lc);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&yempty[bf]);  // this warp is done with chunk c
                 if (tid == 0 && c + kBNB < nch) issue(c + kBNB);
             }
             ycount += (uint32_t)nch;
         };
-        auto nopost = [](int64_t, int) {};
 
         while (stop == STOP_NONE && ok) {
             if (warp < kBNW) {
@@ -368,8 +374,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                                     for (int l = 0; l < lc; ++l)
                                         ff_mac2(as[q], ac[q], yh[l * rb + rr], yl[l * rb + rr], ch[l], cl[l]);
                                 }
-                            },
-                            nopost);
+                            });
 #pragma unroll
                 for (int q = 0; q < kBQR; ++q) {
                     const int64_t r = r_lo + tid + (int64_t)kBNCONS * q;
@@ -385,9 +390,9 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 named_bar(1, kBNCONS);
                 // ---- O1': h_l = Y(:, l)' v1 over this member's rows (per-warp float-float sums,
                 //      warps in order)
-                if (k > 0)
+                if (k > 0) {
                     ystream([&](int64_t, float& hi, float& lo) { hi = lo = 0.f; },
-                            [&](const float* yh, const float* yl, const float*, const float*, int64_t, int lc) {
+                            [&](const float* yh, const float* yl, const float*, const float*, int64_t l0, int lc) {
                                 for (int l = 0; l < lc; ++l) {
                                     float s = 0.f, c = 0.f;
 #pragma unroll
@@ -398,18 +403,19 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                                     }
                                     warp_sum_ff(s, c);
                                     if (lane == 0) {
-                                        wps[warp * kBMaxLC + l] = s;
-                                        wpc[warp * kBMaxLC + l] = c;
+                                        wps[warp * kBMaxD + l0 + l] = s;
+                                        wpc[warp * kBMaxD + l0 + l] = c;
                                     }
                                 }
-                            },
-                            [&](int64_t l0, int lc) {
-                                for (int l = tid; l < lc; l += kBNCONS) {
-                                    float s = wps[l], c = wpc[l];
-                                    for (int w = 1; w < kBNW; ++w) ff_add(s, c, wps[w * kBMaxLC + l], wpc[w * kBMaxLC + l]);
-                                    hacc[l0 + l] = ff_to_double(s, c);
-                                }
                             });
+                    named_bar(1, kBNCONS);  // every warp's partial sums are in
+                    for (int64_t l = tid; l < k; l += kBNCONS) {
+                        float s = wps[l], c = wpc[l];
+                        for (int w = 1; w < kBNW; ++w) ff_add(s, c, wps[w * kBMaxD + l], wpc[w * kBMaxD + l]);
+                        hacc[l] = ff_to_double(s, c);
+                    }
+                    named_bar(1, kBNCONS);  // h is complete before anything reads it
+                }
             }
             if (tm > 1 && k > 0) {
                 // the team's h: every member's partial sums, added in member order
@@ -440,8 +446,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                                     for (int l = 0; l < lc; ++l)
                                         ff_mac2(as[q], ac[q], yh[l * rb + rr], yl[l * rb + rr], ch[l], cl[l]);
                                 }
-                            },
-                            nopost);
+                            });
                 double nrm = 0.0;
 #pragma unroll
                 for (int q = 0; q < kBQR; ++q) {
@@ -733,8 +738,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
 
 template <int P, int CPW, int MT>
 size_t batch_smem() {
-    return (size_t)kBRingBytes + (size_t)(2 * BCfg<P, CPW, MT>::SMAX + kBNB) * 8 + (size_t)2 * kBMaxRows * 4 + (size_t)kBMaxD * 8 +
-           (size_t)2 * kBMaxD * 4 + (size_t)2 * kBNW * kBMaxLC * 4 + (size_t)(4 * kBNW + 16) * 8;
+    return (size_t)kBRingBytes + (size_t)(2 * BCfg<P, CPW, MT>::SMAX + 2 * kBNB) * 8 + (size_t)2 * kBMaxRows * 4 +
+           (size_t)kBMaxD * 8 + (size_t)2 * kBMaxD * 4 + (size_t)2 * kBNW * kBMaxD * 4 + (size_t)(4 * kBNW + 16) * 8;
 }
 
 }  // namespace
