@@ -21,6 +21,11 @@
  *     status of the call that launched the kernels; such a call synchronises `stream`.
  *   - The library is not re-entrant on a single stream for overlapping calls that share a
  *     workspace; distinct workspaces on distinct streams may run concurrently.
+ *   - Scratch that a call allocates itself (stream-ordered, freed on the stream before the call
+ *     returns) comes from a memory pool the library creates per device.  The pool keeps up to
+ *     4 GiB of freed scratch reserved for later calls instead of returning it to the system at
+ *     each synchronisation (mapping it again costs about 1 ms per GB); that reserve is held
+ *     until the process exits.  Entry points that take a workspace use the caller's instead.
  */
 #ifndef RBD_H
 #define RBD_H
@@ -129,7 +134,7 @@ size_t rbd_compress_workspace_bytes(int64_t m, int64_t n, int64_t d_max, rbd_dty
  *  workspace, workspace_bytes
  *          [in]  device scratch of at least rbd_compress_workspace_bytes(m, n, d_max, xt)
  *                bytes, 256-byte aligned; or NULL/0, in which case the call allocates it
- *                stream-ordered (cudaMallocAsync) and frees it before returning.
+ *                stream-ordered from the library's pool and frees it before returning.
  *  stream  [in]  cudaStream_t as void*.
  *  result  [out] host, or NULL: summary (d, stop reason, last indicator, norms of X).
  *
@@ -285,7 +290,7 @@ rbd_status rbd_compress_noalloc(const void* X, rbd_dtype xt, int64_t m, int64_t 
  *  C  [out] device, d x k FP64 column-major, ldc >= d.
  *  d = 0 or k = 0 is a no-op.  Stream-ordered; does not synchronise.  For tall Y the rows are
  *  split across CTAs and a stream-ordered scratch of (splits x d x k) doubles holds the partial
- *  products (allocated with cudaMallocAsync and freed on the stream; if that allocation fails the
+ *  products (allocated from the library's pool and freed on the stream; if that allocation fails the
  *  rows are not split).  Dot products are
  *  evaluated with FP64-grade (float-float, relative error below 2^-44) accuracy.
  *  Errors: RBD_EINVAL for bad sizes/leading dimensions/NULL; RBD_ECUDA on launch failure.
@@ -426,7 +431,7 @@ rbd_status rbd_compress_batched(const rbd_instance* inst, int64_t count, rbd_dty
  *  G       [out] device FP64, m x n, ldg >= m; or NULL to evaluate the loss only.
  *  loss    [out] device, one double: L(X).
  *  stream  [in]  cudaStream_t as void*.  Stream-ordered; allocates its workspace stream-ordered
- *                (cudaMallocAsync) and frees it; does not synchronise.
+ *                (from the library's pool) and frees it; does not synchronise.
  *  Errors: RBD_EINVAL for bad sizes, leading dimensions or NULL arguments; RBD_EUNSUPPORTED for
  *  d > 256; RBD_ENOMEM / RBD_ECUDA on allocation or launch failures.
  */

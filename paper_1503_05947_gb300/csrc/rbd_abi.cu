@@ -305,6 +305,42 @@ uint64_t wait_limit_ns(uint64_t dflt) {
 }
 static thread_local rbd_profile t_profile = {};
 
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64];
+bool g_pool_ready[64] = {};
+}  // namespace
+
+cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool_ready[dev]) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&g_pool[dev], &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = kPoolKeepBytes;
+            e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(g_pool[dev]);
+                return e;
+            }
+            g_pool_ready[dev] = true;
+        }
+        pool = g_pool[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
 rbd_status map_cuda(cudaError_t e) {
     if (e == cudaSuccess) return RBD_OK;
     if (e == cudaErrorMemoryAllocation) return RBD_ENOMEM;
@@ -343,7 +379,7 @@ static rbd_status compress_device(const void* X, rbd_dtype xt, int64_t m, int64_
     bool own = false;
     void* ws = workspace;
     if (ws == nullptr) {
-        ce = cudaMallocAsync(&ws, w.total_bytes, st);
+        ce = lib_malloc_async(&ws, w.total_bytes, st);
         if (ce != cudaSuccess) {
             cudaGetLastError();
             return RBD_ENOMEM;
@@ -612,7 +648,7 @@ rbd_status rbd_compress_rows(const void* X, rbd_dtype xt, int64_t m, int64_t n, 
     cudaStream_t st = (cudaStream_t)stream;
     const int es = elem_bytes((int)xt);
     void* Xt = nullptr;
-    ce = cudaMallocAsync(&Xt, (size_t)m * (size_t)n * es, st);
+    ce = lib_malloc_async(&Xt, (size_t)m * (size_t)n * es, st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return RBD_ENOMEM;
@@ -642,12 +678,12 @@ rbd_status rbd_compress_host(const void* X, rbd_dtype xt, int64_t m, int64_t n, 
     const size_t es = (size_t)elem_bytes((int)xt);
     // device copies: X with its leading dimension m, outputs with compact leading dimensions
     void *dX = nullptr, *dY = nullptr, *dT = nullptr, *dP = nullptr, *dE = nullptr, *dN = nullptr;
-    cudaError_t ce = cudaMallocAsync(&dX, (size_t)m * n * es, st);
-    if (ce == cudaSuccess) ce = cudaMallocAsync(&dY, (size_t)m * d_max * 8, st);
-    if (ce == cudaSuccess) ce = cudaMallocAsync(&dT, (size_t)d_max * n * 8, st);
-    if (ce == cudaSuccess) ce = cudaMallocAsync(&dP, (size_t)d_max * 8, st);
-    if (ce == cudaSuccess) ce = cudaMallocAsync(&dE, (size_t)d_max * 8, st);
-    if (ce == cudaSuccess) ce = cudaMallocAsync(&dN, (size_t)d_max * 8, st);
+    cudaError_t ce = lib_malloc_async(&dX, (size_t)m * n * es, st);
+    if (ce == cudaSuccess) ce = lib_malloc_async(&dY, (size_t)m * d_max * 8, st);
+    if (ce == cudaSuccess) ce = lib_malloc_async(&dT, (size_t)d_max * n * 8, st);
+    if (ce == cudaSuccess) ce = lib_malloc_async(&dP, (size_t)d_max * 8, st);
+    if (ce == cudaSuccess) ce = lib_malloc_async(&dE, (size_t)d_max * 8, st);
+    if (ce == cudaSuccess) ce = lib_malloc_async(&dN, (size_t)d_max * 8, st);
     rbd_status rs = RBD_OK;
     rbd_result res = {};
     if (ce == cudaSuccess)

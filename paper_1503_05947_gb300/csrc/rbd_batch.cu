@@ -1240,8 +1240,8 @@ rbd_status rbd_compress_batched(const rbd_instance* inst, int64_t count, rbd_dty
     cudaStream_t st = (cudaStream_t)stream;
     void* ws = nullptr;
     void* dres = nullptr;
-    cudaError_t ce = cudaMallocAsync(&ws, ws_bytes, st);
-    if (ce == cudaSuccess) ce = cudaMallocAsync(&dres, (size_t)count * sizeof(rbd_batch_result), st);
+    cudaError_t ce = lib_malloc_async(&ws, ws_bytes, st);
+    if (ce == cudaSuccess) ce = lib_malloc_async(&dres, (size_t)count * sizeof(rbd_batch_result), st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         if (ws) cudaFreeAsync(ws, st);

@@ -347,7 +347,7 @@ extern "C" rbd_status rbd_grad(const void* X, rbd_dtype xt, int64_t m, int64_t n
     const size_t b_ep = (size_t)nb * 8;
     const size_t total = b_m1 + b_c + b_cc + b_ep + 64;
     void* ws = nullptr;
-    cudaError_t ce = cudaMallocAsync(&ws, total, st);
+    cudaError_t ce = lib_malloc_async(&ws, total, st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return RBD_ENOMEM;
@@ -448,7 +448,7 @@ extern "C" rbd_status rbd_grad_batched(const rbd_grad_item* items, int64_t count
     }
     cudaStream_t st = (cudaStream_t)stream;
     void* ws = nullptr;
-    cudaError_t ce = cudaMallocAsync(&ws, total, st);
+    cudaError_t ce = lib_malloc_async(&ws, total, st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return RBD_ENOMEM;

@@ -105,7 +105,7 @@ cudaError_t launch_project(const double* Y, int64_t m, int64_t d, int64_t ldy, c
     nsplit = ceil_div(m, rows_per);
     double* part = nullptr;
     if (nsplit > 1) {
-        cudaError_t e = cudaMallocAsync((void**)&part, (size_t)nsplit * d * k * 8, st);
+        cudaError_t e = lib_malloc_async((void**)&part, (size_t)nsplit * d * k * 8, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             part = nullptr;

@@ -207,6 +207,13 @@ struct DeviceState {
     bool ready = false;
 };
 cudaError_t device_state(DeviceState& out);
+
+// Stream-ordered scratch for the calls that allocate: from a memory pool the library creates per
+// device, which keeps up to kPoolKeepBytes of freed memory reserved for the next call (the
+// default pool returns freed memory to the system at every synchronisation, and mapping it again
+// costs ~1 ms per GB).  Freed with cudaFreeAsync.
+constexpr uint64_t kPoolKeepBytes = 4ull << 30;
+cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t st);
 // The storage type of X (RBD_F32_ACC32 stores FP32) and its element size.
 inline int storage_of(int t) { return (t == RBD_F32_ACC32) ? (int)RBD_F32 : t; }
 inline int elem_bytes(int t) { return (t == RBD_F64) ? 8 : (t == RBD_BF16) ? 2 : 4; }
