@@ -27,4 +27,4 @@ from .rbd import (  # noqa: F401
     workspace_bytes,
 )
 from .buildlib import build  # noqa: F401
-from .autograd import RBDLoss, rbd_loss  # noqa: F401
+from .autograd import RBDLoss, RBDLossBatched, rbd_loss, rbd_loss_batched  # noqa: F401

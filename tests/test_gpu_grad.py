@@ -163,3 +163,27 @@ def test_grad_batched_rejects_mixed_outputs(rbd):
                            it["pivots"].data_ptr(), 4, None, 0, 64, g, 64, loss[i:].data_ptr())
     assert lib.rbd_grad_batched(arr, 2, 0, 1.0, 1.0, _stream_ptr(X.device)) == 1  # RBD_EINVAL
     assert lib.rbd_grad_batched(arr, 0, 0, 1.0, 1.0, _stream_ptr(X.device)) == 1
+
+
+def test_batched_autograd_matches_one_by_one(rbd):
+    """rbd_loss_batched (batched compression + batched adjoint behind torch.autograd) against
+    rbd_loss instance by instance: the same pivots, losses to 1e-12 relative, gradients to 1e-10
+    of max |G|; an instance without out-of-sample data and one of another shape in the batch."""
+    host = [c5_instance(i) for i in range(3)]
+    Xs = [to_device(X, torch.float32).clone().requires_grad_(True) for X, _ in host]
+    Xos = [to_device(Xo, torch.float32) for _, Xo in host]
+    Xs.append(to_device(np.asfortranarray(gen.lowrank_haar(300, 200, np.exp(-0.2 * np.arange(200)), seed=77)),
+                        torch.float32).clone().requires_grad_(True))
+    Xos.append(None)
+    Xos[1] = None
+    w = torch.tensor([1.0, 0.5, 2.0, 1.5], dtype=torch.float32, device="cuda")
+    losses = rbd.rbd_loss_batched(Xs, Xos, 24, 1.0, 0.75)
+    assert losses.shape == (4,)
+    (losses * w).sum().backward()
+    for i, (X, Xo) in enumerate(zip(Xs, Xos)):
+        Xr = X.detach().clone().requires_grad_(True)
+        li = rbd.rbd_loss(Xr, Xo, 24, 1.0, 0.75)
+        (li * w[i]).backward()
+        assert abs(losses[i].item() - li.item()) <= 1e-6 * abs(li.item()), i  # FP32 outputs
+        G, Gr = X.grad.double(), Xr.grad.double()
+        assert (G - Gr).abs().max().item() <= 1e-6 * Gr.abs().max().item(), i
