@@ -379,13 +379,17 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                 for (int q = 0; q < kBQR; ++q) {
                     const int64_t r = r_lo + tid + (int64_t)kBNCONS * q;
                     if (r >= r_hi) break;
-                    double v = 0.0;
+                    // v1 = x - Y t in float-float on the FP32 pipes (the FP64 pipe runs at 1/64 rate)
+                    float xh = 0.f, xl = 0.f;
                     if (r < m) {
-                        const double x = (P == 2) ? ((const double*)I.X)[piv * I.ldx + r]
-                                                  : (double)((const float*)I.X)[piv * I.ldx + r];
-                        v = x - ff_to_double(as[q], ac[q]);
+                        if constexpr (P == 2)
+                            split_f64_fast(((const double*)I.X)[piv * I.ldx + r], xh, xl);
+                        else
+                            xh = ((const float*)I.X)[piv * I.ldx + r];
+                        ff_add_acc(xh, xl, -as[q], -ac[q]);
                     }
-                    split_double(v, vh[r], vl[r]);
+                    vh[r] = xh;
+                    vl[r] = xl;
                 }
                 named_bar(1, kBNCONS);
                 // ---- O1': h_l = Y(:, l)' v1 over this member's rows (per-warp float-float sums,
@@ -447,22 +451,28 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
                                         ff_mac2(as[q], ac[q], yh[l * rb + rr], yl[l * rb + rr], ch[l], cl[l]);
                                 }
                             });
-                double nrm = 0.0;
+                // v2 = v1 - Y h and ||v2||^2 in float-float (v2 replaces v1: each thread owns its rows)
+                float ns = 0.f, nc = 0.f;
 #pragma unroll
                 for (int q = 0; q < kBQR; ++q) {
                     const int64_t r = r_lo + tid + (int64_t)kBNCONS * q;
                     if (r >= r_hi) break;
-                    double v = 0.0;
-                    if (r < m) v = ((double)vh[r] + (double)vl[r]) - ff_to_double(as[q], ac[q]);
-                    split_double(v, vh[r], vl[r]);  // v2 replaces v1 (each thread owns its rows)
-                    if (tm > 1) {
-                        I.vbuf[r] = vh[r];
-                        I.vbuf[ldp + r] = vl[r];
+                    float wh = 0.f, wl = 0.f;
+                    if (r < m) {
+                        wh = vh[r];
+                        wl = vl[r];
+                        ff_add_acc(wh, wl, -as[q], -ac[q]);
                     }
-                    nrm += v * v;
+                    vh[r] = wh;
+                    vl[r] = wl;
+                    if (tm > 1) {
+                        I.vbuf[r] = wh;
+                        I.vbuf[ldp + r] = wl;
+                    }
+                    ff_mac2(ns, nc, wh, wl, wh, wl);
                 }
-                nrm = warp_sum_double(nrm);
-                if (lane == 0) red[warp] = nrm;
+                warp_sum_ff(ns, nc);
+                if (lane == 0) red[warp] = ff_to_double(ns, nc);
             }
             ok = __syncthreads_and(ok) != 0;
             if (!ok) break;
@@ -523,11 +533,26 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchParams bp) {
             // ---- xi = v2 / nu: the whole vector for the pass; this member's rows of Y(:, k)
             const double inv_nu = bc[7];
             if (warp < kBNW) {
+                // (vh + vl) / nu in float-float (FP64 only for this member's rows of Y), unless
+                // 1 / nu is outside the FP32 range: then in FP64
+                const bool ffm = inv_nu < 1e38;
+                float ih = 0.f, il = 0.f;
+                if (ffm) split_f64_fast(inv_nu, ih, il);
                 for (int64_t r = tid; r < ldp; r += kBNCONS) {
-                    const double y = ((double)vh[r] + (double)vl[r]) * inv_nu;
-                    split_double(y, vh[r], vl[r]);
+                    double y = 0.0;
+                    if (ffm) {
+                        const float a = vh[r], b = vl[r];
+                        const float p0 = __fmul_rn(a, ih);
+                        float pe = __fmaf_rn(a, ih, -p0);
+                        pe = __fmaf_rn(a, il, pe);
+                        pe = __fmaf_rn(b, ih, pe);
+                        fast_two_sum(p0, pe, vh[r], vl[r]);
+                    } else {
+                        y = ((double)vh[r] + (double)vl[r]) * inv_nu;
+                        split_double(y, vh[r], vl[r]);
+                    }
                     if (r >= r_lo && r < r_hi) {
-                        if (r < m) I.Y[r + k * I.ldy] = y;
+                        if (r < m) I.Y[r + k * I.ldy] = ffm ? (double)vh[r] + (double)vl[r] : y;
                         I.ys[((int64_t)mb * 2 * dmax + k) * rb + (r - r_lo)] = vh[r];
                         I.ys[((int64_t)mb * 2 * dmax + dmax + k) * rb + (r - r_lo)] = vl[r];
                     }
