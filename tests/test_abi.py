@@ -129,3 +129,61 @@ def test_wait_limit_setting_round_trips(lib):
         assert rbd.set_wait_limit(0) == 5000
     finally:
         rbd.set_wait_limit(prev)
+
+
+def _inst(m, n, d_max, tol=1e-3, mode=1, start=0):
+    P = 64  # never dereferenced
+    return rbd_binding._Instance(P, m, n, m, tol, mode, 0, d_max, start, P, m, P, d_max, P, P, None)
+
+
+def test_batched_workspace_and_descriptor_checks(lib):
+    """The batched form's workspace query validates every descriptor on the host: an invalid or
+    out-of-limit matrix gives 0; the size covers every launch shape and grows with d_max."""
+    def ws(*insts, xt=1):
+        arr = (rbd_binding._Instance * len(insts))(*insts)
+        return lib.rbd_batch_workspace_bytes(arr, len(insts), xt)
+
+    small = ws(_inst(300, 200, 20), _inst(1000, 64, 64))
+    assert small >= 4 * (300 * 200 + 1000 * 64)
+    assert ws(_inst(300, 200, 40), _inst(1000, 64, 64)) > small
+    assert ws(_inst(300, 200, 20), xt=0) > ws(_inst(300, 200, 20), xt=1)   # FP64: two planes
+    assert ws(_inst(4097, 64, 8)) == 0       # more than 4096 rows
+    assert ws(_inst(600, 600, 513)) == 0     # d_max above 512
+    assert ws(_inst(300, 200, 201)) == 0     # d_max > min(m, n)
+    assert ws(_inst(300, 200, 20, start=200)) == 0
+    assert ws(_inst(300, 200, 20, tol=-1.0)) == 0
+    assert ws(_inst(300, 200, 20, mode=7)) == 0
+    assert ws(_inst(300, 200, 20), xt=2) == 0  # BF16 is not a batched storage type
+    assert lib.rbd_batch_workspace_bytes(None, 1, 1) == 0
+
+
+def test_adjoint_and_decode_argument_checks(lib):
+    P = ctypes.c_void_p(64)
+    loss = ctypes.c_void_p(128)
+    # rbd_grad: X, m, n, ldx, Y, ldy, T, ldt, pivots, d, Xo, k, ldxo, w_rec, w_proj, G, ldg, loss
+    def g(**kw):
+        a = dict(X=P, m=8, n=6, ldx=8, ldy=8, ldt=4, d=4, wp=1.0)
+        a.update(kw)
+        return lib.rbd_grad(a["X"], 0, a["m"], a["n"], a["ldx"], P, a["ldy"], P, a["ldt"], P, a["d"], None, 0,
+                            a["m"], 1.0, a["wp"], P, a["m"], loss, None)
+
+    assert g(X=None) == 1
+    assert g(ldx=7) == 1
+    assert g(d=7) == 1                 # d > min(m, n)
+    assert g(ldt=3) == 1               # ldt < d
+    assert g(wp=float("nan")) == 1
+    assert g(m=300, n=300, ldx=300, ldy=300, ldt=257, d=257) == 6   # d above 256: unsupported
+    # rbd_grad_batched: count range and a mix of gradient / loss-only outputs, before device work
+    items = (rbd_binding._GradItem * 2)()
+    for i, G in enumerate((P, None)):
+        items[i] = rbd_binding._GradItem(P, 8, 6, 8, P, 8, P, 4, P, 4, None, 0, 8, G, 8, loss)
+    assert lib.rbd_grad_batched(items, 2, 0, 1.0, 1.0, None) == 1
+    assert lib.rbd_grad_batched(items, 0, 0, 1.0, 1.0, None) == 1
+    assert lib.rbd_grad_batched(items, 70000, 0, 1.0, 1.0, None) == 1
+    items[1] = rbd_binding._GradItem(P, 8, 6, 8, P, 8, P, 4, P, 7, None, 0, 8, P, 8, loss)   # d > min(m, n)
+    assert lib.rbd_grad_batched(items, 2, 0, 1.0, 1.0, None) == 1
+    # rbd_reconstruct: n = 0 is a no-op; bad sizes are rejected
+    assert lib.rbd_reconstruct(P, 8, 4, 8, P, 0, 4, P, 8, None) == 0
+    assert lib.rbd_reconstruct(P, 0, 4, 8, P, 5, 4, P, 8, None) == 1
+    assert lib.rbd_reconstruct(P, 8, 4, 7, P, 5, 4, P, 8, None) == 1   # ldy < m
+    assert lib.rbd_reconstruct(P, 8, 4, 8, P, 5, 3, P, 8, None) == 1   # ldt < d
